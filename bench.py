@@ -1,0 +1,329 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the SBP-SAT FDTD leapfrog on GB300.
+
+Workload (default): the 256^3 dielectric-cube block (h = 1 mm, PEC SAT on all
+faces, eps_r = 4 cube of 64^3 cells, Gaussian-derivative dipole at 10 GHz,
+0.95 CFL, 8 probes), FP32.  One "step" = one leapfrog time step (H half-step
+kernel + E half-step kernel) over the whole grid.  Metric: Gcell-updates/s =
+cells * steps / time.  The working set (~470 MB) is larger than L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it is launched under torchrun; every rank advances its own replica
+of the grid (the path has no data-path exchange: replicas only, weak
+scaling) and rank 0 prints the JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_H = 36.0   # per cell: read E (3) + H (3), write H (3), FP32
+BYTES_E = 40.0   # per cell: read H (3) + E (3) + eps_r (1), write E (3), FP32
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--N", type=int, default=256, help="cells per axis of the dielectric workload")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) > 8:
+                for nm, v in zip(names, r[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_digest():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2206_00638_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        with open(path) as f:
+            rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    except OSError:
+        return None
+    digest = csrc_digest()
+    for r in rows:
+        if len(r) >= 4 and r[0] == kernel and r[1] == digest:
+            return float(r[3])          # bytes per launch, scaled to the bench workload
+    return None
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2206_00638_gb300 import sbpsat
+    from paper_2206_00638_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    w = wl.dielectric(N=args.N, steps=args.steps)
+    spec = w.blocks[0]
+    cells = spec.n[0] * spec.n[1] * spec.n[2]
+    stream = torch.cuda.current_stream()
+    sim = sbpsat.from_workload(w, stream=stream)[0]
+    sim.reserve_probes(args.warmup + 2 * args.steps + 8)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    # headline: K whole steps, device-timed with CUDA events on the simulation's stream
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        sim.step(args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = cells * args.steps * world / (ms_max * 1e-3) / 1e9
+
+    # per-kernel durations: the same steps issued as half-steps with events around each launch
+    nk = min(args.steps, 400)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2 * nk)]
+    sims = [sim]
+    for q in range(nk):
+        ev[2 * q][0].record(stream)
+        sbpsat.half_step_h(sims)
+        ev[2 * q][1].record(stream)
+        ev[2 * q + 1][0].record(stream)
+        sbpsat.half_step_e(sims)
+        ev[2 * q + 1][1].record(stream)
+    torch.cuda.synchronize()
+    th = sum(ev[2 * q][0].elapsed_time(ev[2 * q][1]) for q in range(nk)) / nk
+    te = sum(ev[2 * q + 1][0].elapsed_time(ev[2 * q + 1][1]) for q in range(nk)) / nk
+    peak, peak_kind = peaks()
+    dom, tdom, bdom = ("e_update", te, BYTES_E) if te >= th else ("h_update", th, BYTES_H)
+    achieved = bdom * cells / (tdom * 1e-3) / 1e9
+    sim.close()
+
+    # end to end through the public API with host buffers: create (materials up),
+    # initial fields up, K steps, probes and one field down
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.zeros(wl.field_shape(spec.n, c), dtype=torch.float32).pin_memory() for c in range(6)]
+        out = torch.empty(pinned[2].shape, dtype=torch.float32).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = sbpsat.Sim(spec.n, spec.h, spec.faces, eps_r=spec.eps_r, cfl=w.cfl, stream=stream)
+        for c in range(6):
+            sbpsat._check(sbpsat.lib().sbp_set_field(s2.handle, c, pinned[c].data_ptr(), 0), "set")
+        for src in spec.sources:
+            s2.add_source(src.comp, src.i, src.j, src.k, src.kind, src.amp, src.tw, src.t0, src.f)
+        for p in spec.probes:
+            s2.add_probe(p.comp, p.i, p.j, p.k)
+        s2.reserve_probes(args.steps)
+        s2.step(args.steps)
+        pr = s2.probes()
+        sbpsat._check(sbpsat.lib().sbp_get_field(s2.handle, 2, out.data_ptr(), 0), "get")
+        t1 = time.perf_counter()
+        h2d = sum(p.numel() * 4 for p in pinned) + cells * 4
+        d2h = out.numel() * 4 + pr.size * 4
+        e2e = {"value": cells * args.steps / (t1 - t0) / 1e9, "unit": "Gcell-updates/s",
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "seconds": t1 - t0}
+        s2.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args, budget=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": "Gcell-updates/s", "value": value, "unit": "Gcell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": "PEC x6",
+                       "cfl": w.cfl, "precision": "FP32", "parallelism": f"replicas x{world}",
+                       "l2": "inputs_larger_than_l2 (~470 MB working set)"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": recorded_traffic(dom), "algorithmic_bytes_per_cell": bdom,
+                         "ms_h_update": th, "ms_e_update": te},
+            "e2e": e2e,
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, budget=15.0):
+    """The FP64 oracle, as it stands, on the host cores: full-size grid, as many
+    steps as fit in the time budget (bounded sample)."""
+    import oracle
+    from paper_2206_00638_gb300 import workloads as wl
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    w = wl.dielectric(N=args.N, steps=args.steps)
+    spec = w.blocks[0]
+    dt = oracle.dt_cfl(w.cfl, *spec.h)
+    blk = oracle.Block(spec.n, spec.h, dt, spec.faces, eps_r=spec.eps_r)
+    for s in spec.sources:
+        blk.add_source(s.comp, s.i, s.j, s.k, s.kind, s.amp, s.tw, s.t0, s.f)
+    cells = spec.n[0] * spec.n[1] * spec.n[2]
+    t0 = time.perf_counter()
+    oracle.step([blk], 1)
+    t1 = time.perf_counter()
+    n = max(1, min(args.steps, int(budget / max(t1 - t0, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step([blk], n)
+    t1 = time.perf_counter()
+    return {"value": cells * n / (t1 - t0) / 1e9, "unit": "Gcell-updates/s", "cores": oracle.get_threads(),
+            "kind": "oracle", "sample": f"{n} leapfrog steps of the full {w.name} grid (FP64 C oracle)",
+            "seconds": t1 - t0}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    budget = 150.0
+    import oracle
+    from paper_2206_00638_gb300 import workloads as wl
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    w = wl.dielectric(N=args.N, steps=args.steps)
+    spec = w.blocks[0]
+    dt = oracle.dt_cfl(w.cfl, *spec.h)
+    blk = oracle.Block(spec.n, spec.h, dt, spec.faces, eps_r=spec.eps_r)
+    for s in spec.sources:
+        blk.add_source(s.comp, s.i, s.j, s.k, s.kind, s.amp, s.tw, s.t0, s.f)
+    cells = spec.n[0] * spec.n[1] * spec.n[2]
+    tw0 = time.perf_counter()
+    nw = max(1, min(args.warmup, 3))
+    oracle.step([blk], nw)
+    per = (time.perf_counter() - tw0) / nw
+    k = max(1, min(args.steps, int(budget / max(per, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.step([blk], k)
+    t1 = time.perf_counter()
+    value = cells * k / (t1 - t0) / 1e9
+    line = {
+        "impl": "reference", "metric": "Gcell-updates/s", "value": value, "unit": "Gcell-updates/s",
+        "n_gpus": 0, "steps": k, "warmup": nw, "ms_per_step": (t1 - t0) / k * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "cells": cells, "precision": "FP64"},
+        "cpu_baseline": {"value": value, "unit": "Gcell-updates/s", "cores": oracle.get_threads(),
+                         "kind": "oracle",
+                         "sample": f"{k} of the requested {args.steps} steps of the full {w.name} grid"},
+        "e2e": {"value": value, "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * sbpsat.h -- C ABI of the GB300 SBP-SAT FDTD library (arXiv 2206.00638).
+ *
+ * The library advances Maxwell's equations on a Cartesian block with the
+ * paper's staggered summation-by-parts operators and SAT boundary penalties,
+ * leapfrog in time, on one CUDA GPU.  Every call is plain C: sizes, host or
+ * device pointers and a cudaStream_t passed as void*.  No PyTorch types.
+ *
+ * Conventions shared by all calls
+ *   - Return value: SBP_OK (0) or a negative SBP_E* code; sbp_strerror()
+ *     names it.  A failed call leaves the simulation unchanged unless noted.
+ *   - Components: SBP_EX..SBP_HZ = 0..5.  Each component lives on the node
+ *     grid of Table I of the paper: along an axis with n cells a component
+ *     has n+1 nodes on the "plus" grid x+ = {x_0..x_n} or n+2 nodes on the
+ *     "minus" grid x- = {x_0, x_1/2, ..., x_{n-1/2}, x_n} (Sec. II-A).
+ *       Ex: (x-, y+, z+)  Ey: (x+, y-, z+)  Ez: (x+, y+, z-)
+ *       Hx: (x+, y-, z-)  Hy: (x-, y+, z-)  Hz: (x-, y-, z+)
+ *     Host-visible field arrays use these natural extents, x fastest, e.g.
+ *     Ex has (nx+2)*(ny+1)*(nz+1) entries (array dimensions of Sec. V).
+ *   - Element type of field, probe-sample and initial-field buffers is the
+ *     simulation's arithmetic type: float for SBP_FP32 and
+ *     SBP_FP32_FP16STORE, double for SBP_FP64.
+ *   - Faces are numbered x-, x+, y-, y+, z-, z+ (0..5).
+ *   - Units are SI: metres, seconds, V/m, A/m, A/m^2.
+ *   - Calls are asynchronous on the simulation's stream unless stated.
+ *     Host buffers passed to asynchronous calls are copied before return.
+ */
+#ifndef SBPSAT_H
+#define SBPSAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define SBP_OK 0
+#define SBP_EINVAL (-1)          /* bad argument (size, index, enum, NULL)           */
+#define SBP_ENOMEM (-2)          /* device or host allocation failed                 */
+#define SBP_ECUDA (-3)           /* a CUDA runtime call failed                       */
+#define SBP_EUNSTABLE (-4)       /* energy monitor saw growth or a non-finite value  */
+#define SBP_ETIMEOUT (-5)        /* a bounded device wait gave up                    */
+#define SBP_ENOTCONFORMING (-6)  /* interface faces do not share their node sets     */
+#define SBP_ESTATE (-7)          /* call not valid in the current state              */
+#define SBP_ECAPACITY (-8)       /* buffer too small (probes, workspace)             */
+
+typedef enum { SBP_PEC = 0, SBP_PMC = 1, SBP_ABSORBING = 2, SBP_INTERFACE = 3 } sbp_face_t;
+typedef enum { SBP_FP32 = 0, SBP_FP64 = 1, SBP_FP32_FP16STORE = 2 } sbp_precision_t;
+typedef enum { SBP_EX = 0, SBP_EY = 1, SBP_EZ = 2, SBP_HX = 3, SBP_HY = 4, SBP_HZ = 5 } sbp_comp_t;
+typedef enum { SBP_GAUSS = 0, SBP_GAUSS_DERIV = 1, SBP_MOD_GAUSS = 2 } sbp_waveform_t;
+
+#define SBP_FLAG_ALLOW_UNSTABLE 1  /* accept cfl_fraction > 1 (for stability tests) */
+
+/* Problem statement of one block (Sec. V: a cavity of nx*ny*nz cells; Sec. VI:
+ * mesh size, materials, walls, dt at a fraction of the CFL limit). */
+typedef struct sbp_grid_desc {
+    int32_t nx, ny, nz;      /* cells per axis, each >= 4 (the closures of D+ and D- must
+                                not overlap: Appendix)                                    */
+    double dx, dy, dz;       /* mesh steps, metres, > 0                                    */
+    const float *eps_r;      /* relative permittivity per cell, host, nx*ny*nz, x fastest,
+                                values >= 1e-3; NULL = vacuum.  Node values are the mean
+                                over the cells whose closed box contains the node.         */
+    const float *mu_r;       /* relative permeability per cell, same layout; NULL = 1      */
+    int32_t face[6];         /* sbp_face_t per face; SBP_INTERFACE faces must be joined
+                                with sbp_connect before the first step                    */
+    double cfl_fraction;     /* dt = cfl / (c0 sqrt(1/dx^2+1/dy^2+1/dz^2)), 0 < cfl <= 1
+                                (the FDTD limit, which the paper shows is also the
+                                SBP-SAT limit: Sec. VI-A)                                 */
+    int32_t precision;       /* sbp_precision_t                                            */
+    int32_t energy_every;    /* >0: compute the FP64 energy every that many steps during
+                                sbp_step and flag growth (sbp_energy_series); 0 = off      */
+    int32_t flags;           /* SBP_FLAG_*                                                  */
+} sbp_grid_desc;
+
+typedef struct sbp_sim sbp_sim;
+
+/* Create a simulation: validates the descriptor, allocates the six field
+ * arrays (zero), the material arrays and the probe/energy buffers on the
+ * current CUDA device, and builds the node coefficients on the device.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream); all later
+ * work of this simulation runs on it.  *out receives the handle, owned by the
+ * caller until sbp_destroy.  Errors: SBP_EINVAL, SBP_ENOMEM, SBP_ECUDA. */
+int sbp_create(const sbp_grid_desc *desc, void *cuda_stream, sbp_sim **out);
+
+/* Device bytes sbp_create_in needs for this descriptor (fields, materials,
+ * reduction scratch), or 0 if the descriptor is invalid. */
+size_t sbp_workspace_bytes(const sbp_grid_desc *desc);
+
+/* As sbp_create, but every device array is carved from the caller's device
+ * buffer dev_workspace (>= sbp_workspace_bytes, 256-byte aligned), which the
+ * caller keeps alive until sbp_destroy.  Lets a caching allocator own the
+ * memory.  Errors: as sbp_create, SBP_ECAPACITY if bytes is too small. */
+int sbp_create_in(const sbp_grid_desc *desc, void *cuda_stream, void *dev_workspace,
+                  size_t bytes, sbp_sim **out);
+
+/* Join face face_a of a to face face_b of b by the conforming interface SAT:
+ * the zero-phase periodic SAT of Eqs. (EPBC1)-(EPBC6) with the +-1/2
+ * coefficients of Eq. (EPBCP), coupling the two blocks' tangential fields.
+ * The faces must be normal to the same axis, of opposite sides, and have
+ * equal transverse cell counts and spacings (else SBP_ENOTCONFORMING); a
+ * block may be joined to itself (periodic with zero phase).  Both faces are
+ * set to SBP_INTERFACE.  Coupled blocks must be advanced together with
+ * sbp_step_group and share one stream. */
+int sbp_connect(sbp_sim *a, int face_a, sbp_sim *b, int face_b);
+
+/* Copy one component (natural extents, x fastest) into the simulation.
+ * src: host pointer (is_device = 0, copied before return) or device pointer
+ * (is_device = 1, read asynchronously on the simulation's stream). */
+int sbp_set_field(sbp_sim *s, int comp, const void *src, int is_device);
+
+/* Copy one component out (natural extents).  to_device = 0: dst is host
+ * memory and the call synchronises the stream; 1: device pointer, async. */
+int sbp_get_field(sbp_sim *s, int comp, void *dst, int to_device);
+
+/* Add a soft current-density source J = amp * w(t) (A/m^2) on E component
+ * comp at node (i, j, k) of that component's grid: eps dE/dt = curl H - J.
+ * An index of -1 selects every node along that axis (e.g. i = j = -1 gives
+ * a sheet on plane k).  Waveforms (Sec. VI-B, VI-C):
+ *   SBP_GAUSS        exp(-4 pi (t-t0)^2 / tw^2)
+ *   SBP_GAUSS_DERIV  its time derivative scaled to unit peak
+ *   SBP_MOD_GAUSS    sin(2 pi f t) exp(-4 pi (t-t0)^2 / tw^2)
+ * J is evaluated at t^{n+1/2} in the E half-step.  At most 16 sources.
+ * Returns the source index (>= 0) or a negative code. */
+int sbp_add_source(sbp_sim *s, int comp, int i, int j, int k, int waveform, double amp,
+                   double tw, double t0, double f);
+
+/* Add a point probe on component comp at node (i, j, k) of its grid.
+ * Sample n of a probe is H^{n+1/2} (H components) or E^{n+1} (E
+ * components) of step n counted from the last sbp_reserve_probes.
+ * At most 64 probes.  *probe_id receives its index. */
+int sbp_add_probe(sbp_sim *s, int comp, int i, int j, int k, int *probe_id);
+
+/* (Re)allocate the device probe buffer for nsteps samples per probe and
+ * restart sample counting at the current step. */
+int sbp_reserve_probes(sbp_sim *s, int64_t nsteps);
+
+/* Advance nsteps leapfrog steps (H half-step, then E half-step with sources
+ * and probes), asynchronously on the stream.  For a simulation joined to
+ * others use sbp_step_group. */
+int sbp_step(sbp_sim *s, int64_t nsteps);
+
+/* Advance nsims coupled simulations together: each step runs every H
+ * half-step, then every E half-step, so interfaces read consistent levels.
+ * All must share one stream. */
+int sbp_step_group(sbp_sim **sims, int nsims, int64_t nsteps);
+
+/* One half of a leapfrog step for nsims coupled simulations (one stream):
+ * sbp_half_step_h forms H^{n+1/2} from E^n (Eqs. (10)-(15), Alg. 2, probes
+ * of H components); sbp_half_step_e forms E^{n+1} from H^{n+1/2}
+ * (Eqs. (7)-(9), (19)-(21), Alg. 1, sources, probes of E components) and
+ * advances the step counter.  They let a caller interleave its own work
+ * between the half-steps (for instance a face-plane exchange with another
+ * device); sbp_step == sbp_half_step_h then sbp_half_step_e per step.  The
+ * energy monitor of desc.energy_every runs inside sbp_half_step_h. */
+int sbp_half_step_h(sbp_sim **sims, int nsims);
+int sbp_half_step_e(sbp_sim **sims, int nsims);
+
+/* Copy probe samples to host: out[p * cap + n] for probe p, sample n < cap.
+ * Synchronises the stream.  *nsamples (optional) receives the number of
+ * samples recorded per probe. */
+int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples);
+
+/* FP64 discrete energy W^n = 1/2 [sum_E eps P''' (E^n)^2 +
+ * sum_H mu P''' H^{n-1/2} H^{n+1/2}] (Eq. (16) in the form leapfrog
+ * conserves; H^{n+1/2} is formed on the fly, fields are not changed).
+ * Synchronous.  For coupled blocks use sbp_energy_group. */
+int sbp_energy(sbp_sim *s, double *W);
+int sbp_energy_group(sbp_sim **sims, int nsims, double *W);
+
+/* Energy samples taken every desc.energy_every steps during sbp_step:
+ * out[m] = W at step m * energy_every.  Synchronises.  Returns
+ * SBP_EUNSTABLE if a sample is non-finite or exceeds 1.5x the first one
+ * (after copying what fits). */
+int sbp_energy_series(sbp_sim *s, double *out, int64_t cap, int64_t *count);
+
+/* Wait for all work on the simulation's stream. */
+int sbp_sync(sbp_sim *s);
+
+double sbp_dt(const sbp_sim *s);           /* time step in seconds            */
+int64_t sbp_step_index(const sbp_sim *s);  /* steps taken since creation      */
+int sbp_destroy(sbp_sim *s);               /* frees everything the sim owns   */
+const char *sbp_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBPSAT_H */

@@ -377,6 +377,7 @@ static void sat_terms(const ob_block *b, int c, const int idx[3], double eps_r, 
     int isH = c >= HX;
     for (int f = 0; f < 6; f++) {
         int ax = f / 2, side = (f % 2) ? +1 : -1;
+        if (idx[ax] != 0 && idx[ax] != ext(b, c, ax) - 1) continue;   /* not on this face */
         int s; int p = partner(c, ax, &s);
         if (p < 0) continue;                     /* c is normal to this face */
         /* the tangential field on a face sits on the end nodes of its grid */

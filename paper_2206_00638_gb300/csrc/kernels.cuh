@@ -1,0 +1,615 @@
+// Device code of the GB300 SBP-SAT FDTD library (arXiv 2206.00638).
+//
+// Two fused kernels advance one leapfrog step:
+//   h_update  H^{n+1/2} = H^{n-1/2} + dt/mu (D- E^n) + SAT_H     Eqs. (10)-(15), Alg. 2
+//   e_update  E^{n+1}   = E^n + dt/eps (D+ H^{n+1/2} - J) + SAT_E Eqs. (7)-(9), (19)-(21), Alg. 1
+// Each thread owns one (i, j) column of nodes and marches up a chunk of z
+// planes (2.5D blocking): the z-neighbour needed by the staggered difference
+// is carried in a register from the previous plane, x/y neighbours come from
+// L1.  Interior nodes (every index in [3, n-2]) take a branch-free fast path
+// with the two-point stencil; the three boundary layers of each axis take the
+// general path, which evaluates the closure rows of D+ / D- (Appendix), the
+// SAT penalties of the face type (PEC / PMC / absorbing / interface), point
+// and sheet sources and probes.  The fast/general choice is uniform per warp
+// except in the two x-edge warps of a row.
+//
+// FP32 arithmetic keeps its coefficients exact to ~1e-14: every material
+// coefficient dt/(eps h) is carried as an unevaluated sum hi + lo of two
+// floats, and the node's 1/sum(eps_r) as a Newton-corrected reciprocal pair,
+// so rounding of a coefficient does not bias the phase velocity; only the
+// per-step rounding of the field update (unbiased) remains.
+#pragma once
+#include <cstdint>
+#include <type_traits>
+
+namespace sbp {
+
+constexpr int kMaxSources = 16;
+constexpr int kMaxProbes = 64;
+constexpr int kBlockX = 32;
+constexpr int kBlockY = 8;
+
+enum : int { kPEC = 0, kPMC = 1, kABS = 2, kIFACE = 3 };
+
+// Table I: component c lives on the plus grid (n+1 nodes) along axis a.
+__host__ __device__ constexpr bool on_plus(int c, int a)
+{
+    return c == 0 ? a != 0 : c == 1 ? a != 1 : c == 2 ? a != 2
+         : c == 3 ? a == 0 : c == 4 ? a == 1 : a == 2;
+}
+
+// Eqs. (7)-(12): dC/dt = (+1) D^{axis0} C0 + (-1) D^{axis1} C1.
+__host__ __device__ constexpr int curl_comp(int c, int t)
+{
+    // Ex: Hz, Hy   Ey: Hx, Hz   Ez: Hy, Hx   Hx: Ey, Ez   Hy: Ez, Ex   Hz: Ex, Ey
+    return t == 0 ? (c == 0 ? 5 : c == 1 ? 3 : c == 2 ? 4 : c == 3 ? 1 : c == 4 ? 2 : 0)
+                  : (c == 0 ? 4 : c == 1 ? 5 : c == 2 ? 3 : c == 3 ? 2 : c == 4 ? 0 : 1);
+}
+__host__ __device__ constexpr int curl_axis(int c, int t)
+{
+    // Ex: y, z   Ey: z, x   Ez: x, y   Hx: z, y   Hy: x, z   Hz: y, x
+    return t == 0 ? (c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 0 : c == 3 ? 2 : c == 4 ? 0 : 1)
+                  : (c == 0 ? 2 : c == 1 ? 0 : c == 2 ? 1 : c == 3 ? 1 : c == 4 ? 2 : 0);
+}
+__host__ __device__ constexpr int curl_sign(int t) { return t == 0 ? 1 : -1; }
+
+template <typename T> struct Coef { T hi, lo; };
+
+struct Link {               // interface partner of one face
+    const void *F[6];       // partner block's padded fields
+    long long sy, sz;       // partner strides (elements)
+    int n_norm;             // partner cell count along the face normal
+    int side;               // partner face side: -1 low, +1 high
+};
+
+struct Src { int comp, i, j, k, wf; double amp, tw, t0, f; };
+struct Prb { int comp, i, j, k; };
+
+template <typename T>
+struct Params {
+    T *F[6];                // padded fields Ex..Hz: element (i,j,k) at k*sz + j*sy + i
+    const float *eps;       // ghost-padded cell eps_r on the same layout: cell (cx,cy,cz) at (cx+1,cy+1,cz+1)
+    const float *mu;        // same for mu_r (only read when MUVAR)
+    int n[3];
+    long long sy, sz;
+    int face[6];
+    Link link[6];
+    Coef<T> B[3];           // H: dt/(mu0 h_a) (uniform mu) or 2 dt/(mu0 h_a) (scaled by 1/sum2 mu_r)
+    Coef<T> A[3];           // E: 4 dt/(eps0 h_a), scaled by 1/sum4 eps_r of the node
+    Coef<T> AJ;             // 4 dt/eps0, source term
+    double dt, eta0, eps0, mu0;
+    double h[3];
+    int nsrc, nprb;
+    Src src[kMaxSources];
+    Prb prb[kMaxProbes];
+    T *probe_buf;
+    long long probe_cap, probe_slot;   // sample slot of this step (skip if >= cap)
+    long long step;                    // n: the E half-step injects J(t^{n+1/2})
+    double *partials;                  // energy partial sums, one per CTA of h_update
+    int kchunk;
+};
+
+// ---------------------------------------------------------------------------
+// small arithmetic helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(const Coef<float> &c, float x, float scale = 1.f)
+    {
+        hi = fmaf(scale * c.hi, x, hi);
+        lo = fmaf(scale * c.lo, x, lo);
+    }
+};
+template <> struct Acc<double> {
+    double hi = 0.0;
+    __device__ __forceinline__ void add(const Coef<double> &c, double x, double scale = 1.0)
+    {
+        hi = fma(scale * c.hi, x, hi);
+    }
+};
+
+// Reciprocal of s as hi + lo (hardware approximation + one Newton residual).
+__device__ __forceinline__ void recip_pair(float s, float &rh, float &rl)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+    float e = fmaf(-s, r, 1.0f);
+    rh = r;
+    rl = r * e;
+}
+
+// increment = r * acc with r = 1/s (E nodes, or H nodes with varying mu)
+__device__ __forceinline__ float scaled_increment(const Acc<float> &a, float s)
+{
+    float rh, rl;
+    recip_pair(s, rh, rl);
+    return fmaf(rh, a.hi, fmaf(rh, a.lo, rl * a.hi));
+}
+__device__ __forceinline__ double scaled_increment(const Acc<double> &a, double s)
+{
+    return a.hi / s;
+}
+__device__ __forceinline__ float plain_increment(const Acc<float> &a) { return a.hi + a.lo; }
+__device__ __forceinline__ double plain_increment(const Acc<double> &a) { return a.hi; }
+
+// Rows of the Appendix operators at unit spacing.  u points at node 0 of the
+// line, s is the stride along the axis, r the output row, n the cell count.
+// D- : x+ (n+1 values) -> x- (n+2 rows).
+template <typename T>
+__device__ __forceinline__ T dminus_row(const T *__restrict__ u, long long s, int r, int n)
+{
+    if (r == 0) return u[s] - u[0];
+    if (r == 2) return (T(4) * u[2 * s] - T(3) * u[s] - u[0]) * T(0.2);
+    if (r == n - 1) return (u[n * s] + T(3) * u[(n - 1) * s] - T(4) * u[(n - 2) * s]) * T(0.2);
+    if (r == n + 1) return u[n * s] - u[(n - 1) * s];
+    return u[r * s] - u[(r - 1) * s];          // rows 1, 3..n-2, n
+}
+// D+ : x- (n+2 values) -> x+ (n+1 rows).
+template <typename T>
+__device__ __forceinline__ T dplus_row(const T *__restrict__ v, long long s, int r, int n)
+{
+    if (r == 0) return T(0.5) * (v[s] + v[2 * s]) - v[0];
+    if (r == 1) return T(0.75) * v[2 * s] - T(0.5) * v[0] - T(0.25) * v[s];
+    if (r == n - 1) return T(0.25) * v[n * s] + T(0.5) * v[(n + 1) * s] - T(0.75) * v[(n - 1) * s];
+    if (r == n) return v[(n + 1) * s] - T(0.5) * (v[(n - 1) * s] + v[n * s]);
+    return v[(r + 1) * s] - v[r * s];          // rows 2..n-2
+}
+
+// 1D norm weight (unit spacing) of node r: P+ = diag(1/2,1,...,1,1/2),
+// P- = diag(1/2,1/4,5/4,1,...,1,5/4,1/4,1/2)  (Appendix).
+__device__ __forceinline__ double norm_weight(bool plus, int r, int n)
+{
+    if (plus) return (r == 0 || r == n) ? 0.5 : 1.0;
+    if (r == 0 || r == n + 1) return 0.5;
+    if (r == 1 || r == n) return 0.25;
+    if (r == 2 || r == n - 1) return 1.25;
+    return 1.0;
+}
+
+__device__ __forceinline__ int extent(const int n[3], int c, int a) { return n[a] + (on_plus(c, a) ? 1 : 2); }
+
+// Sum of the ghost-padded cell values around a node of component c: the
+// closed-box cell set of the node, always 2x2 (E) or 2x1 (H) entries after
+// ghost padding (duplicates stand for clipped cells, so the mean is the mean
+// over the distinct cells).
+template <int C, typename S = float>
+__device__ __forceinline__ S cell_sum(const float *__restrict__ m, long long o, long long sy, long long sz)
+{
+    // ghost-padded index of the node's first cell is the node index itself;
+    // a plus-grid axis spans two cells (offset 0 and +1), a minus-grid axis one.
+    constexpr bool px = on_plus(C, 0), py = on_plus(C, 1), pz = on_plus(C, 2);
+    S s = S(__ldg(m + o));
+    if (px) s += S(__ldg(m + o + 1));
+    if (py) s += S(__ldg(m + o + sy));
+    if (pz) s += S(__ldg(m + o + sz));
+    if (px && py) s += S(__ldg(m + o + 1 + sy));
+    if (px && pz) s += S(__ldg(m + o + 1 + sz));
+    if (py && pz) s += S(__ldg(m + o + sy + sz));
+    return s;
+}
+// number of entries summed by cell_sum<C>
+__host__ __device__ constexpr int cell_count(int c)
+{
+    return (on_plus(c, 0) ? 2 : 1) * (on_plus(c, 1) ? 2 : 1) * (on_plus(c, 2) ? 2 : 1);
+}
+
+// Source waveforms (Sec. VI-B, VI-C): t and t0, tw in seconds.
+__device__ __forceinline__ double waveform(int wf, double t, double tw, double t0, double f)
+{
+    const double x = (t - t0) / tw;
+    const double g = exp(-4.0 * 3.14159265358979323846 * x * x);
+    if (wf == 0) return g;
+    if (wf == 1) return -5.0132565492620005 * x * 1.6487212707001282 * g;   // -sqrt(8 pi) x e^{1/2} g
+    double ph = f * t;
+    ph -= floor(ph);
+    return sin(6.283185307179586 * ph) * g;
+}
+
+template <typename T>
+__device__ __forceinline__ bool probe_here(const Params<T> &p, unsigned long long mask, int k)
+{
+    while (mask) {
+        int q = __ffsll(mask) - 1;
+        mask &= mask - 1;
+        if (p.prb[q].k == k) return true;
+    }
+    return false;
+}
+template <typename T>
+__device__ __forceinline__ bool source_here(const Params<T> &p, unsigned mask, int k)
+{
+    while (mask) {
+        int q = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (p.src[q].k == k || p.src[q].k < 0) return true;
+    }
+    return false;
+}
+template <typename T>
+__device__ __forceinline__ void write_probes(const Params<T> &p, unsigned long long mask, int c, int k, T v)
+{
+    while (mask) {
+        int q = __ffsll(mask) - 1;
+        mask &= mask - 1;
+        if (p.prb[q].comp == c && p.prb[q].k == k && p.probe_slot < p.probe_cap)
+            p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = v;
+    }
+}
+
+// Block-wide deterministic sum of one double per thread (fixed tree).
+__device__ __forceinline__ void block_sum_to(double v, double *dst)
+{
+    __shared__ double red[kBlockX * kBlockY / 32];
+    const int lane = threadIdx.x, warp = threadIdx.y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < (int)blockDim.y ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) *dst = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// H half-step: general path for one component at one node
+// ---------------------------------------------------------------------------
+template <typename T, int C, bool MUVAR>
+__device__ __forceinline__ T h_node(const Params<T> &p, const int idx[3], long long o, T hold)
+{
+    Acc<T> acc;
+    T gam = T(0);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int u = curl_comp(C, t), a = curl_axis(C, t), sg = curl_sign(t);
+        const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
+        const T *line = p.F[u] + (o - idx[a] * st);
+        const T d = dminus_row(line, st, idx[a], p.n[a]);
+        acc.add(p.B[a], d, T(sg));
+        // H on the minus grid along a: face nodes at 0 and n+1 carry the SAT
+        if (idx[a] == 0 || idx[a] == p.n[a] + 1) {
+            const int side = idx[a] == 0 ? -1 : 1;
+            const int f = 2 * a + (side > 0);
+            const int type = p.face[f];
+            if (type != kPMC) {
+                const T phi = T(-sg * side);
+                const T pv = line[(side < 0 ? 0 : p.n[a]) * st];
+                if (type == kPEC) {
+                    acc.add(p.B[a], pv, T(2) * phi);
+                } else if (type == kABS) {
+                    acc.add(p.B[a], pv, phi);
+                    const T er = cell_sum<C, T>(p.eps, o, p.sy, p.sz) * T(0.5);
+                    const T mr = MUVAR ? cell_sum<C, T>(p.mu, o, p.sy, p.sz) * T(0.5) : T(1);
+                    const T eta = T(p.eta0) * sqrt(mr / er);
+                    // gamma = dt eta / (2 mu h_a); B holds dt/(mu0 h_a) (x2 when mu varies)
+                    const T ba = MUVAR ? T(p.B[a].hi) * T(0.5) / mr : T(p.B[a].hi);
+                    gam += T(0.5) * ba * eta;
+                } else {   // interface: (phi/2)(E^A - E^B) / (mu w), w = h/2
+                    const Link &L = p.link[f];
+                    const T *nf = static_cast<const T *>(L.F[u]);
+                    const int nidx = L.side < 0 ? 0 : L.n_norm;      // partner E on its plus grid along a
+                    long long on = 0;
+                    const long long ost[3] = {1, L.sy, L.sz};
+                    for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
+                    acc.add(p.B[a], pv - nf[on], phi);
+                }
+            }
+        }
+    }
+    T inc;
+    if (MUVAR) {
+        inc = scaled_increment(acc, cell_sum<C, T>(p.mu, o, p.sy, p.sz));
+    } else {
+        inc = plain_increment(acc);
+    }
+    if (gam != T(0)) return ((T(1) - gam) * hold + inc) / (T(1) + gam);
+    return hold + inc;
+}
+
+// E half-step: general path for one component at one node.
+template <typename T, int C, bool MUVAR>
+__device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long long o, T eold,
+                                    unsigned smask, double t_half)
+{
+    Acc<T> acc;
+    T gam = T(0);
+    const T se = cell_sum<C, T>(p.eps, o, p.sy, p.sz);     // 4 * eps_r(node)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int u = curl_comp(C, t), a = curl_axis(C, t), sg = curl_sign(t);
+        const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
+        const T *line = p.F[u] + (o - idx[a] * st);
+        const T d = dplus_row(line, st, idx[a], p.n[a]);
+        acc.add(p.A[a], d, T(sg));
+        // E on the plus grid along a: face nodes at 0 and n carry the SAT
+        if (idx[a] == 0 || idx[a] == p.n[a]) {
+            const int side = idx[a] == 0 ? -1 : 1;
+            const int f = 2 * a + (side > 0);
+            const int type = p.face[f];
+            if (type != kPEC) {
+                const T phi = T(-sg * side);
+                const T pv = line[(side < 0 ? 0 : p.n[a] + 1) * st];
+                if (type == kPMC) {
+                    acc.add(p.A[a], pv, T(2) * phi);
+                } else if (type == kABS) {
+                    acc.add(p.A[a], pv, phi);
+                    const T er = se * T(0.25);
+                    const T mr = MUVAR ? cell_sum<C, T>(p.mu, o, p.sy, p.sz) * T(0.25) : T(1);
+                    const T eta = T(p.eta0) * sqrt(mr / er);
+                    // gamma = dt / (2 eta eps h_a) = (4 dt/(eps0 h_a)) / (4 eps_r) / (2 eta)
+                    gam += T(p.A[a].hi) / se / (T(2) * eta);
+                } else {
+                    const Link &L = p.link[f];
+                    const T *nf = static_cast<const T *>(L.F[u]);
+                    const int nidx = L.side < 0 ? 0 : L.n_norm + 1;  // partner H on its minus grid along a
+                    long long on = 0;
+                    const long long ost[3] = {1, L.sy, L.sz};
+                    for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
+                    acc.add(p.A[a], pv - nf[on], phi);
+                }
+            }
+        }
+    }
+    // current-density sources: eps dE/dt = ... - J
+    unsigned m = smask;
+    while (m) {
+        const int q = __ffs(m) - 1;
+        m &= m - 1;
+        const Src &S = p.src[q];
+        if (S.comp == C && (S.k < 0 || S.k == idx[2])) {
+            const double J = S.amp * waveform(S.wf, t_half, S.tw, S.t0, S.f);
+            acc.add(p.AJ, T(J), T(-1));
+        }
+    }
+    const T inc = scaled_increment(acc, se);
+    if (gam != T(0)) return ((T(1) - gam) * eold + inc) / (T(1) + gam);
+    return eold + inc;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+// Per-thread masks of the probes / sources whose (i, j) match this column.
+template <typename T>
+__device__ __forceinline__ void column_masks(const Params<T> &p, int i, int j, bool want_h,
+                                             unsigned long long &pm, unsigned &sm)
+{
+    pm = 0ull;
+    sm = 0u;
+    for (int q = 0; q < p.nprb; ++q)
+        if (p.prb[q].i == i && p.prb[q].j == j && ((p.prb[q].comp >= 3) == want_h)) pm |= 1ull << q;
+    if (!want_h)
+        for (int q = 0; q < p.nsrc; ++q)
+            if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) sm |= 1u << q;
+}
+
+// H half-step.  ENERGY: also accumulate the leapfrog energy of Eq. (16) into
+// p.partials (FP64); STORE: write H^{n+1/2} (false = energy query only).
+template <typename T, bool ENERGY, bool STORE, bool MUVAR>
+__global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T> p)
+{
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    const int k0 = blockIdx.z * p.kchunk;
+    const int k1 = min(k0 + p.kchunk, nz + 2);
+    double wacc = 0.0;
+    if (i < nx + 2 && j < ny + 2) {
+        T *__restrict__ Hx = p.F[3];
+        T *__restrict__ Hy = p.F[4];
+        T *__restrict__ Hz = p.F[5];
+        const T *__restrict__ Ex = p.F[0];
+        const T *__restrict__ Ey = p.F[1];
+        const T *__restrict__ Ez = p.F[2];
+        unsigned long long pm;
+        unsigned sm;
+        column_masks(p, i, j, true, pm, sm);
+        const bool xyin = i >= 3 && i <= nx - 2 && j >= 3 && j <= ny - 2;
+        const Coef<T> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
+        long long o = (long long)k0 * p.sz + (long long)j * p.sy + i;
+        T exm = k0 > 0 ? __ldg(Ex + o - p.sz) : T(0);
+        T eym = k0 > 0 ? __ldg(Ey + o - p.sz) : T(0);
+        for (int k = k0; k < k1; ++k, o += p.sz) {
+            const T exc = __ldg(Ex + o);
+            const T eyc = __ldg(Ey + o);
+            const bool fast = !ENERGY && !MUVAR && xyin && k >= 3 && k <= nz - 2 && !(pm && probe_here(p, pm, k));
+            if (fast) {
+                const T ezc = __ldg(Ez + o);
+                const T ex_jm = __ldg(Ex + o - p.sy);
+                const T ey_im = __ldg(Ey + o - 1);
+                const T ez_im = __ldg(Ez + o - 1);
+                const T ez_jm = __ldg(Ez + o - p.sy);
+                const T dEy_z = eyc - eym, dEz_y = ezc - ez_jm;
+                const T dEz_x = ezc - ez_im, dEx_z = exc - exm;
+                const T dEx_y = exc - ex_jm, dEy_x = eyc - ey_im;
+                Acc<T> ax, ay, az;
+                ax.add(Bz, dEy_z); ax.add(By, dEz_y, T(-1));
+                ay.add(Bx, dEz_x); ay.add(Bz, dEx_z, T(-1));
+                az.add(By, dEx_y); az.add(Bx, dEy_x, T(-1));
+                Hx[o] = Hx[o] + plain_increment(ax);
+                Hy[o] = Hy[o] + plain_increment(ay);
+                Hz[o] = Hz[o] + plain_increment(az);
+            } else {
+                const int idx[3] = {i, j, k};
+                // Hx (x+, y-, z-)
+                if (i <= nx && j <= ny + 1 && k <= nz + 1) {
+                    const T ho = Hx[o];
+                    const T hn = h_node<T, 3, MUVAR>(p, idx, o, ho);
+                    if (STORE) Hx[o] = hn;
+                    if (STORE && pm) write_probes(p, pm, 3, k, hn);
+                    if (ENERGY) {
+                        const double w = norm_weight(true, i, nx) * norm_weight(false, j, ny) * norm_weight(false, k, nz);
+                        const double mr = MUVAR ? 0.5 * cell_sum<3, double>(p.mu, o, p.sy, p.sz) : 1.0;
+                        wacc += p.mu0 * mr * w * (double)ho * (double)hn;
+                    }
+                }
+                // Hy (x-, y+, z-)
+                if (i <= nx + 1 && j <= ny && k <= nz + 1) {
+                    const T ho = Hy[o];
+                    const T hn = h_node<T, 4, MUVAR>(p, idx, o, ho);
+                    if (STORE) Hy[o] = hn;
+                    if (STORE && pm) write_probes(p, pm, 4, k, hn);
+                    if (ENERGY) {
+                        const double w = norm_weight(false, i, nx) * norm_weight(true, j, ny) * norm_weight(false, k, nz);
+                        const double mr = MUVAR ? 0.5 * cell_sum<4, double>(p.mu, o, p.sy, p.sz) : 1.0;
+                        wacc += p.mu0 * mr * w * (double)ho * (double)hn;
+                    }
+                }
+                // Hz (x-, y-, z+)
+                if (i <= nx + 1 && j <= ny + 1 && k <= nz) {
+                    const T ho = Hz[o];
+                    const T hn = h_node<T, 5, MUVAR>(p, idx, o, ho);
+                    if (STORE) Hz[o] = hn;
+                    if (STORE && pm) write_probes(p, pm, 5, k, hn);
+                    if (ENERGY) {
+                        const double w = norm_weight(false, i, nx) * norm_weight(false, j, ny) * norm_weight(true, k, nz);
+                        const double mr = MUVAR ? 0.5 * cell_sum<5, double>(p.mu, o, p.sy, p.sz) : 1.0;
+                        wacc += p.mu0 * mr * w * (double)ho * (double)hn;
+                    }
+                }
+                if (ENERGY) {
+                    // E^n part: eps P''' E^2 at this node position for every E component present
+                    if (i <= nx + 1 && j <= ny && k <= nz) {   // Ex (x-, y+, z+)
+                        const double w = norm_weight(false, i, nx) * norm_weight(true, j, ny) * norm_weight(true, k, nz);
+                        wacc += p.eps0 * 0.25 * cell_sum<0, double>(p.eps, o, p.sy, p.sz) * w * (double)exc * (double)exc;
+                    }
+                    if (i <= nx && j <= ny + 1 && k <= nz) {   // Ey (x+, y-, z+)
+                        const double w = norm_weight(true, i, nx) * norm_weight(false, j, ny) * norm_weight(true, k, nz);
+                        wacc += p.eps0 * 0.25 * cell_sum<1, double>(p.eps, o, p.sy, p.sz) * w * (double)eyc * (double)eyc;
+                    }
+                    if (i <= nx && j <= ny && k <= nz + 1) {   // Ez (x+, y+, z-)
+                        const double w = norm_weight(true, i, nx) * norm_weight(true, j, ny) * norm_weight(false, k, nz);
+                        const T ezc = __ldg(Ez + o);
+                        wacc += p.eps0 * 0.25 * cell_sum<2, double>(p.eps, o, p.sy, p.sz) * w * (double)ezc * (double)ezc;
+                    }
+                }
+            }
+            exm = exc;
+            eym = eyc;
+        }
+    }
+    if (ENERGY) {
+        const double hvol = p.h[0] * p.h[1] * p.h[2];
+        block_sum_to(wacc * hvol, p.partials + ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x);
+    }
+}
+
+// E half-step with sources (J at t^{n+1/2}) and E probes.
+template <typename T, bool MUVAR>
+__global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T> p)
+{
+    const int i = blockIdx.x * kBlockX + threadIdx.x;
+    const int j = blockIdx.y * kBlockY + threadIdx.y;
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    const int k0 = blockIdx.z * p.kchunk;
+    const int k1 = min(k0 + p.kchunk, nz + 2);
+    if (i >= nx + 2 || j >= ny + 2) return;
+    T *__restrict__ Ex = p.F[0];
+    T *__restrict__ Ey = p.F[1];
+    T *__restrict__ Ez = p.F[2];
+    const T *__restrict__ Hx = p.F[3];
+    const T *__restrict__ Hy = p.F[4];
+    const T *__restrict__ Hz = p.F[5];
+    const float *__restrict__ eps = p.eps;
+    unsigned long long pm;
+    unsigned sm;
+    column_masks(p, i, j, false, pm, sm);
+    const bool xyin = i >= 3 && i <= nx - 2 && j >= 3 && j <= ny - 2;
+    const Coef<T> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
+    const double t_half = ((double)p.step + 0.5) * p.dt;
+    long long o = (long long)k0 * p.sz + (long long)j * p.sy + i;
+    // plane-k carries: Hx, Hy at (i,j,k) and eps at the four cells (i..i+1, j..j+1, k)
+    T hxc = __ldg(Hx + o), hyc = __ldg(Hy + o);
+    float f00 = __ldg(eps + o), f10 = __ldg(eps + o + 1), f01 = __ldg(eps + o + p.sy), f11 = __ldg(eps + o + 1 + p.sy);
+    for (int k = k0; k < k1; ++k, o += p.sz) {
+        const bool fast = xyin && k >= 3 && k <= nz - 2 && !(pm && probe_here(p, pm, k)) && !(sm && source_here(p, sm, k));
+        // next plane (k+1) always exists inside the padded array for k <= nz
+        const bool has_next = k + 1 < nz + 2;
+        const T hxn = has_next ? __ldg(Hx + o + p.sz) : T(0);
+        const T hyn = has_next ? __ldg(Hy + o + p.sz) : T(0);
+        const float e00 = has_next ? __ldg(eps + o + p.sz) : 0.f;
+        const float e10 = has_next ? __ldg(eps + o + p.sz + 1) : 0.f;
+        const float e01 = has_next ? __ldg(eps + o + p.sz + p.sy) : 0.f;
+        const float e11 = has_next ? __ldg(eps + o + p.sz + p.sy + 1) : 0.f;
+        if (fast) {
+            const T hzc = __ldg(Hz + o);
+            const T hz_jp = __ldg(Hz + o + p.sy);
+            const T hz_ip = __ldg(Hz + o + 1);
+            const T hx_jp = __ldg(Hx + o + p.sy);
+            const T hy_ip = __ldg(Hy + o + 1);
+            Acc<T> ax, ay, az;
+            ax.add(Ay, hz_jp - hzc); ax.add(Az, hyn - hyc, T(-1));
+            ay.add(Az, hxn - hxc);   ay.add(Ax, hz_ip - hzc, T(-1));
+            az.add(Ax, hy_ip - hyc); az.add(Ay, hx_jp - hxc, T(-1));
+            const float sx = (f00 + f01) + (e00 + e01);
+            const float sy = (f00 + f10) + (e00 + e10);
+            const float sz = (f00 + f10) + (f01 + f11);
+            Ex[o] = Ex[o] + scaled_increment(ax, T(sx));
+            Ey[o] = Ey[o] + scaled_increment(ay, T(sy));
+            Ez[o] = Ez[o] + scaled_increment(az, T(sz));
+        } else {
+            const int idx[3] = {i, j, k};
+            if (i <= nx + 1 && j <= ny && k <= nz) {          // Ex (x-, y+, z+)
+                const T en = e_node<T, 0, MUVAR>(p, idx, o, Ex[o], sm, t_half);
+                Ex[o] = en;
+                if (pm) write_probes(p, pm, 0, k, en);
+            }
+            if (i <= nx && j <= ny + 1 && k <= nz) {          // Ey (x+, y-, z+)
+                const T en = e_node<T, 1, MUVAR>(p, idx, o, Ey[o], sm, t_half);
+                Ey[o] = en;
+                if (pm) write_probes(p, pm, 1, k, en);
+            }
+            if (i <= nx && j <= ny && k <= nz + 1) {          // Ez (x+, y+, z-)
+                const T en = e_node<T, 2, MUVAR>(p, idx, o, Ez[o], sm, t_half);
+                Ez[o] = en;
+                if (pm) write_probes(p, pm, 2, k, en);
+            }
+        }
+        hxc = hxn; hyc = hyn;
+        f00 = e00; f10 = e10; f01 = e01; f11 = e11;
+    }
+}
+
+// Fixed-order sum of the per-CTA energy partials (one CTA, deterministic).
+__global__ void __launch_bounds__(256) energy_finalize(const double *__restrict__ partials, long long n,
+                                                        double *__restrict__ out)
+{
+    __shared__ double red[256];
+    double v = 0.0;
+    for (long long q = threadIdx.x; q < n; q += 256) v += partials[q];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 0.5 * red[0];
+}
+
+// Ghost-padded cell array (coefficient build, once per grid): padded (cx+1,
+// cy+1, cz+1) holds cell (cx, cy, cz); ghost layers repeat the nearest cell.
+__global__ void pad_cells(const float *__restrict__ cells, int nx, int ny, int nz, float fill,
+                          float *__restrict__ out, long long sy, long long sz)
+{
+    const long long total = (long long)(nx + 2) * (ny + 2) * (nz + 2);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % (nx + 2));
+        const int j = (int)((q / (nx + 2)) % (ny + 2));
+        const int k = (int)(q / ((long long)(nx + 2) * (ny + 2)));
+        float v = fill;
+        if (cells) {
+            const int cx = min(max(i - 1, 0), nx - 1);
+            const int cy = min(max(j - 1, 0), ny - 1);
+            const int cz = min(max(k - 1, 0), nz - 1);
+            v = cells[((long long)cz * ny + cy) * nx + cx];
+        }
+        out[(long long)k * sz + (long long)j * sy + i] = v;
+    }
+}
+
+}  // namespace sbp

@@ -1,0 +1,649 @@
+// Host side of the C ABI declared in include/sbpsat.h: validation, memory
+// layout, coefficient build and kernel launches of the SBP-SAT FDTD leapfrog.
+//
+// Memory layout in HBM: every field (and the ghost-padded eps_r / mu_r cell
+// arrays) uses one common padded shape (nz+2) x (ny+2) x pitch, pitch =
+// nx+2 rounded up to 8 elements so each row starts on a 32-byte sector, plus
+// one slack plane so that +1 / +row / +plane neighbour reads of the last
+// plane stay inside the allocation.  One linear offset o = k*sz + j*sy + i
+// addresses node (i, j, k) of every component; positions outside a
+// component's natural extents (Table I) stay zero.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sbpsat.h"
+#include "kernels.cuh"
+
+namespace {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct sbp_sim {
+    int prec = SBP_FP32;
+    int n[3] = {0, 0, 0};
+    double h[3] = {0, 0, 0};
+    double dt = 0;
+    int face[6] = {0, 0, 0, 0, 0, 0};
+    int energy_every = 0;
+    int flags = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    size_t esize = 4;
+    long long sy = 0, sz = 0;
+    size_t field_elems = 0;               // elements per padded array, slack included
+    void *F[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    float *eps = nullptr;
+    float *mu = nullptr;
+    double *partials = nullptr;
+    long long npartials = 0;
+    double *escalar = nullptr;
+    sbp_sim *nbr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int nbr_face[6] = {-1, -1, -1, -1, -1, -1};
+    std::vector<sbp::Src> src;
+    std::vector<sbp::Prb> prb;
+    void *probe_buf = nullptr;
+    long long probe_cap = 0, probe_base = 0;
+    double *eseries = nullptr;
+    long long eseries_cap = 0, eseries_count = 0;
+    long long step = 0;
+    void *workspace = nullptr;
+    bool own_ws = false;
+    int kchunk = 8;
+    dim3 grid;
+};
+
+namespace {
+
+struct Layout {
+    long long sy, sz;
+    size_t field_elems;
+    size_t esize;
+    size_t field_bytes, cell_bytes, partial_bytes;
+    long long npartials;
+    int kchunk;
+    dim3 grid;
+    size_t total;
+};
+
+bool desc_valid(const sbp_grid_desc *d)
+{
+    if (!d) return false;
+    if (d->nx < 4 || d->ny < 4 || d->nz < 4) return false;
+    if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0)) return false;
+    if (!(d->cfl_fraction > 0)) return false;
+    if (d->cfl_fraction > 1.0 && !(d->flags & SBP_FLAG_ALLOW_UNSTABLE)) return false;
+    if (d->precision != SBP_FP32 && d->precision != SBP_FP64) return false;
+    for (int f = 0; f < 6; f++)
+        if (d->face[f] < SBP_PEC || d->face[f] > SBP_INTERFACE) return false;
+    if (d->energy_every < 0) return false;
+    const long long cells = (long long)d->nx * d->ny * d->nz;
+    if (cells > (1ll << 34)) return false;
+    for (const float *m : {d->eps_r, d->mu_r}) {
+        if (!m) continue;
+        for (long long q = 0; q < cells; q++)
+            if (!(m[q] >= 1e-3f) || !std::isfinite(m[q])) return false;
+    }
+    return true;
+}
+
+Layout make_layout(const sbp_grid_desc *d)
+{
+    Layout L;
+    L.esize = d->precision == SBP_FP64 ? 8 : 4;
+    L.sy = (long long)round_up((size_t)d->nx + 2, 8);
+    L.sz = L.sy * (d->ny + 2);
+    L.field_elems = (size_t)L.sz * (d->nz + 3);          // nz+2 planes + one slack plane
+    L.field_bytes = round_up(L.field_elems * L.esize, 256);
+    L.cell_bytes = round_up(L.field_elems * sizeof(float), 256);
+    const int gx = (d->nx + 2 + sbp::kBlockX - 1) / sbp::kBlockX;
+    const int gy = (d->ny + 2 + sbp::kBlockY - 1) / sbp::kBlockY;
+    // enough z-chunks to fill the GPU several times over, at least 8 planes each
+    const long long planes = d->nz + 2;
+    const long long want_gz = std::max(1ll, (4 * 152 * 4 + (long long)gx * gy - 1) / ((long long)gx * gy));
+    int kc = (int)std::max(8ll, (planes + want_gz - 1) / want_gz);
+    if (const char *env = std::getenv("SBP_KCHUNK")) {
+        const int v = std::atoi(env);
+        if (v > 0) kc = v;
+    }
+    L.kchunk = kc;
+    const int gz = (int)((planes + kc - 1) / kc);
+    L.grid = dim3(gx, gy, gz);
+    L.npartials = (long long)gx * gy * gz;
+    L.partial_bytes = round_up((size_t)L.npartials * sizeof(double), 256);
+    L.total = 6 * L.field_bytes + L.cell_bytes * (d->mu_r ? 2 : 1) + L.partial_bytes + 256;
+    return L;
+}
+
+int cuda_fail(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return SBP_ENOMEM;
+    return SBP_ECUDA;
+}
+
+#define SBP_CUDA(call)                          \
+    do {                                        \
+        cudaError_t e_ = (call);                \
+        if (e_ != cudaSuccess) return cuda_fail(e_); \
+    } while (0)
+
+int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
+{
+    s->prec = d->precision;
+    s->n[0] = d->nx; s->n[1] = d->ny; s->n[2] = d->nz;
+    s->h[0] = d->dx; s->h[1] = d->dy; s->h[2] = d->dz;
+    s->dt = d->cfl_fraction / (kC0 * std::sqrt(1.0 / (d->dx * d->dx) + 1.0 / (d->dy * d->dy) + 1.0 / (d->dz * d->dz)));
+    for (int f = 0; f < 6; f++) s->face[f] = d->face[f];
+    s->energy_every = d->energy_every;
+    s->flags = d->flags;
+    s->esize = L.esize;
+    s->sy = L.sy; s->sz = L.sz;
+    s->field_elems = L.field_elems;
+    s->kchunk = L.kchunk;
+    s->grid = L.grid;
+    s->npartials = L.npartials;
+    char *p = ws;
+    for (int c = 0; c < 6; c++) { s->F[c] = p; p += L.field_bytes; }
+    s->eps = reinterpret_cast<float *>(p); p += L.cell_bytes;
+    if (d->mu_r) { s->mu = reinterpret_cast<float *>(p); p += L.cell_bytes; }
+    s->partials = reinterpret_cast<double *>(p); p += L.partial_bytes;
+    s->escalar = reinterpret_cast<double *>(p);
+
+    // coefficient build (a1): ghost-padded cell arrays on the device.  The
+    // caller's cells are staged through the (still unused) Hx array.
+    const size_t ncell = (size_t)d->nx * d->ny * d->nz;
+    const int threads = 256;
+    const int blocks = (int)std::min<long long>(4096, (L.field_elems + threads - 1) / threads);
+    for (int m = 0; m < 2; m++) {
+        const float *host = m == 0 ? d->eps_r : d->mu_r;
+        float *dst = m == 0 ? s->eps : s->mu;
+        if (m == 1 && !d->mu_r) break;
+        float *stage = nullptr;
+        if (host) {
+            stage = static_cast<float *>(s->F[3]);
+            SBP_CUDA(cudaMemcpyAsync(stage, host, ncell * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+        }
+        SBP_CUDA(cudaMemsetAsync(dst, 0, L.field_elems * sizeof(float), s->stream));
+        sbp::pad_cells<<<blocks, threads, 0, s->stream>>>(stage, d->nx, d->ny, d->nz, 1.0f, dst, L.sy, L.sz);
+        SBP_CUDA(cudaGetLastError());
+        SBP_CUDA(cudaStreamSynchronize(s->stream));   // host cells may be released after return
+    }
+    for (int c = 0; c < 6; c++) SBP_CUDA(cudaMemsetAsync(s->F[c], 0, L.field_elems * L.esize, s->stream));
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    return SBP_OK;
+}
+
+template <typename T>
+sbp::Coef<T> split(double v)
+{
+    sbp::Coef<T> c;
+    c.hi = (T)v;
+    c.lo = (T)(v - (double)c.hi);
+    return c;
+}
+
+template <typename T>
+int make_params(const sbp_sim *s, sbp::Params<T> &p)
+{
+    std::memset(&p, 0, sizeof(p));
+    for (int c = 0; c < 6; c++) p.F[c] = static_cast<T *>(s->F[c]);
+    p.eps = s->eps;
+    p.mu = s->mu;
+    for (int a = 0; a < 3; a++) p.n[a] = s->n[a];
+    p.sy = s->sy;
+    p.sz = s->sz;
+    for (int f = 0; f < 6; f++) {
+        p.face[f] = s->face[f];
+        if (s->face[f] == SBP_INTERFACE) {
+            const sbp_sim *nb = s->nbr[f];
+            if (!nb) return SBP_ESTATE;
+            for (int c = 0; c < 6; c++) p.link[f].F[c] = nb->F[c];
+            p.link[f].sy = nb->sy;
+            p.link[f].sz = nb->sz;
+            p.link[f].n_norm = nb->n[f / 2];
+            p.link[f].side = (s->nbr_face[f] % 2) ? 1 : -1;
+        }
+    }
+    const double bscale = s->mu ? 2.0 : 1.0;
+    for (int a = 0; a < 3; a++) {
+        p.B[a] = split<T>(bscale * s->dt / (kMu0 * s->h[a]));
+        p.A[a] = split<T>(4.0 * s->dt / (kEps0 * s->h[a]));
+        p.h[a] = s->h[a];
+    }
+    p.AJ = split<T>(4.0 * s->dt / kEps0);
+    p.dt = s->dt;
+    p.eta0 = std::sqrt(kMu0 / kEps0);
+    p.eps0 = kEps0;
+    p.mu0 = kMu0;
+    p.nsrc = (int)s->src.size();
+    for (int q = 0; q < p.nsrc; q++) p.src[q] = s->src[q];
+    p.nprb = (int)s->prb.size();
+    for (int q = 0; q < p.nprb; q++) p.prb[q] = s->prb[q];
+    p.probe_buf = static_cast<T *>(s->probe_buf);
+    p.probe_cap = s->probe_buf ? s->probe_cap : 0;
+    p.probe_slot = s->step - s->probe_base;
+    p.step = s->step;
+    p.partials = s->partials;
+    p.kchunk = s->kchunk;
+    return SBP_OK;
+}
+
+template <typename T>
+int launch_h(const sbp_sim *s, bool energy, bool store)
+{
+    sbp::Params<T> p;
+    int rc = make_params<T>(s, p);
+    if (rc) return rc;
+    const dim3 block(sbp::kBlockX, sbp::kBlockY);
+    const bool muv = s->mu != nullptr;
+    if (!energy) {
+        if (muv) sbp::h_update<T, false, true, true><<<s->grid, block, 0, s->stream>>>(p);
+        else sbp::h_update<T, false, true, false><<<s->grid, block, 0, s->stream>>>(p);
+    } else if (store) {
+        if (muv) sbp::h_update<T, true, true, true><<<s->grid, block, 0, s->stream>>>(p);
+        else sbp::h_update<T, true, true, false><<<s->grid, block, 0, s->stream>>>(p);
+    } else {
+        if (muv) sbp::h_update<T, true, false, true><<<s->grid, block, 0, s->stream>>>(p);
+        else sbp::h_update<T, true, false, false><<<s->grid, block, 0, s->stream>>>(p);
+    }
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+template <typename T>
+int launch_e(const sbp_sim *s)
+{
+    sbp::Params<T> p;
+    int rc = make_params<T>(s, p);
+    if (rc) return rc;
+    const dim3 block(sbp::kBlockX, sbp::kBlockY);
+    if (s->mu) sbp::e_update<T, true><<<s->grid, block, 0, s->stream>>>(p);
+    else sbp::e_update<T, false><<<s->grid, block, 0, s->stream>>>(p);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+int launch_h_any(const sbp_sim *s, bool energy, bool store)
+{
+    return s->prec == SBP_FP64 ? launch_h<double>(s, energy, store) : launch_h<float>(s, energy, store);
+}
+int launch_e_any(const sbp_sim *s)
+{
+    return s->prec == SBP_FP64 ? launch_e<double>(s) : launch_e<float>(s);
+}
+
+int finalize_energy(const sbp_sim *s, double *dst)
+{
+    sbp::energy_finalize<<<1, 256, 0, s->stream>>>(s->partials, s->npartials, dst);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+int ensure_series(sbp_sim *s, long long need)
+{
+    if (need <= s->eseries_cap) return SBP_OK;
+    long long cap = std::max(need, 2 * s->eseries_cap + 16);
+    double *nb = nullptr;
+    SBP_CUDA(cudaMalloc(&nb, cap * sizeof(double)));
+    if (s->eseries && s->eseries_count > 0)
+        SBP_CUDA(cudaMemcpyAsync(nb, s->eseries, s->eseries_count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->eseries) cudaFree(s->eseries);
+    s->eseries = nb;
+    s->eseries_cap = cap;
+    return SBP_OK;
+}
+
+int extents_of(const sbp_sim *s, int comp, int e[3])
+{
+    if (comp < 0 || comp > 5) return SBP_EINVAL;
+    for (int a = 0; a < 3; a++) e[a] = s->n[a] + (sbp::on_plus(comp, a) ? 1 : 2);
+    return SBP_OK;
+}
+
+int create_common(const sbp_grid_desc *d, void *stream, void *ws, size_t bytes, bool own, sbp_sim **out)
+{
+    if (!out || !desc_valid(d)) return SBP_EINVAL;
+    *out = nullptr;
+    Layout L = make_layout(d);
+    sbp_sim *s = new (std::nothrow) sbp_sim();
+    if (!s) return SBP_ENOMEM;
+    cudaGetDevice(&s->device);
+    s->stream = static_cast<cudaStream_t>(stream);
+    if (own) {
+        cudaError_t e = cudaMalloc(&ws, L.total);
+        if (e != cudaSuccess) { delete s; return cuda_fail(e); }
+        s->own_ws = true;
+    } else {
+        if (!ws || bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) { delete s; return ws ? SBP_ECAPACITY : SBP_EINVAL; }
+    }
+    s->workspace = ws;
+    int rc = setup(s, d, L, static_cast<char *>(ws));
+    if (rc) { if (s->own_ws) cudaFree(ws); delete s; return rc; }
+    *out = s;
+    return SBP_OK;
+}
+
+int check_group(sbp_sim **sims, int nsims)
+{
+    if (!sims || nsims <= 0) return SBP_EINVAL;
+    for (int q = 0; q < nsims; q++) {
+        if (!sims[q]) return SBP_EINVAL;
+        if (sims[q]->stream != sims[0]->stream) return SBP_EINVAL;
+        for (int f = 0; f < 6; f++)
+            if (sims[q]->face[f] == SBP_INTERFACE && !sims[q]->nbr[f]) return SBP_ESTATE;
+    }
+    cudaSetDevice(sims[0]->device);
+    return SBP_OK;
+}
+
+int half_h(sbp_sim **sims, int nsims)
+{
+    for (int q = 0; q < nsims; q++) {
+        sbp_sim *s = sims[q];
+        const bool mon = s->energy_every > 0 && (s->step % s->energy_every) == 0;
+        if (mon) {
+            int rc = ensure_series(s, s->step / s->energy_every + 1);
+            if (rc) return rc;
+        }
+        int rc = launch_h_any(s, mon, true);
+        if (rc) return rc;
+        if (mon) {
+            rc = finalize_energy(s, s->eseries + s->step / s->energy_every);
+            if (rc) return rc;
+            s->eseries_count = s->step / s->energy_every + 1;
+        }
+    }
+    return SBP_OK;
+}
+
+int half_e(sbp_sim **sims, int nsims)
+{
+    for (int q = 0; q < nsims; q++) {
+        int rc = launch_e_any(sims[q]);
+        if (rc) return rc;
+    }
+    for (int q = 0; q < nsims; q++) sims[q]->step++;
+    return SBP_OK;
+}
+
+int step_group(sbp_sim **sims, int nsims, int64_t nsteps)
+{
+    if (nsteps < 0) return SBP_EINVAL;
+    int rc = check_group(sims, nsims);
+    if (rc) return rc;
+    for (int q = 0; q < nsims; q++) {
+        sbp_sim *s = sims[q];
+        if (s->energy_every > 0) {
+            rc = ensure_series(s, (s->step + nsteps) / s->energy_every + 1);
+            if (rc) return rc;
+        }
+    }
+    for (int64_t t = 0; t < nsteps; t++) {
+        rc = half_h(sims, nsims);
+        if (rc) return rc;
+        rc = half_e(sims, nsims);
+        if (rc) return rc;
+    }
+    return SBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sbp_workspace_bytes(const sbp_grid_desc *desc)
+{
+    if (!desc_valid(desc)) return 0;
+    return make_layout(desc).total;
+}
+
+int sbp_create(const sbp_grid_desc *desc, void *cuda_stream, sbp_sim **out)
+{
+    return create_common(desc, cuda_stream, nullptr, 0, true, out);
+}
+
+int sbp_create_in(const sbp_grid_desc *desc, void *cuda_stream, void *dev_workspace, size_t bytes, sbp_sim **out)
+{
+    return create_common(desc, cuda_stream, dev_workspace, bytes, false, out);
+}
+
+int sbp_connect(sbp_sim *a, int fa, sbp_sim *b, int fb)
+{
+    if (!a || !b || fa < 0 || fa > 5 || fb < 0 || fb > 5) return SBP_EINVAL;
+    if (a->prec != b->prec || a->stream != b->stream) return SBP_EINVAL;
+    const int ax = fa / 2;
+    if (fb / 2 != ax || (fa % 2) == (fb % 2)) return SBP_ENOTCONFORMING;
+    for (int t = 0; t < 3; t++) {
+        if (t == ax) continue;
+        if (a->n[t] != b->n[t] || a->h[t] != b->h[t]) return SBP_ENOTCONFORMING;
+    }
+    if (a->dt != b->dt) return SBP_ENOTCONFORMING;
+    a->face[fa] = SBP_INTERFACE; a->nbr[fa] = b; a->nbr_face[fa] = fb;
+    b->face[fb] = SBP_INTERFACE; b->nbr[fb] = a; b->nbr_face[fb] = fa;
+    return SBP_OK;
+}
+
+int sbp_set_field(sbp_sim *s, int comp, const void *src, int is_device)
+{
+    int e[3];
+    if (!s || !src || extents_of(s, comp, e)) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    cudaMemcpy3DParms m = {};
+    m.srcPtr = make_cudaPitchedPtr(const_cast<void *>(src), e[0] * s->esize, e[0] * s->esize, e[1]);
+    m.dstPtr = make_cudaPitchedPtr(s->F[comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
+    m.extent = make_cudaExtent(e[0] * s->esize, e[1], e[2]);
+    m.kind = cudaMemcpyDefault;
+    SBP_CUDA(cudaMemcpy3DAsync(&m, s->stream));
+    if (!is_device) SBP_CUDA(cudaStreamSynchronize(s->stream));
+    return SBP_OK;
+}
+
+int sbp_get_field(sbp_sim *s, int comp, void *dst, int to_device)
+{
+    int e[3];
+    if (!s || !dst || extents_of(s, comp, e)) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    cudaMemcpy3DParms m = {};
+    m.srcPtr = make_cudaPitchedPtr(s->F[comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
+    m.dstPtr = make_cudaPitchedPtr(dst, e[0] * s->esize, e[0] * s->esize, e[1]);
+    m.extent = make_cudaExtent(e[0] * s->esize, e[1], e[2]);
+    m.kind = cudaMemcpyDefault;
+    SBP_CUDA(cudaMemcpy3DAsync(&m, s->stream));
+    if (!to_device) SBP_CUDA(cudaStreamSynchronize(s->stream));
+    return SBP_OK;
+}
+
+int sbp_add_source(sbp_sim *s, int comp, int i, int j, int k, int waveform, double amp, double tw, double t0, double f)
+{
+    int e[3];
+    if (!s || comp < 0 || comp > 2 || extents_of(s, comp, e)) return SBP_EINVAL;
+    if ((int)s->src.size() >= sbp::kMaxSources) return SBP_ECAPACITY;
+    if (waveform < SBP_GAUSS || waveform > SBP_MOD_GAUSS || !(tw > 0)) return SBP_EINVAL;
+    const int idx[3] = {i, j, k};
+    for (int a = 0; a < 3; a++)
+        if (idx[a] < -1 || idx[a] >= e[a]) return SBP_EINVAL;
+    sbp::Src q;
+    q.comp = comp; q.i = i; q.j = j; q.k = k; q.wf = waveform;
+    q.amp = amp; q.tw = tw; q.t0 = t0; q.f = f;
+    s->src.push_back(q);
+    return (int)s->src.size() - 1;
+}
+
+int sbp_add_probe(sbp_sim *s, int comp, int i, int j, int k, int *probe_id)
+{
+    int e[3];
+    if (!s || extents_of(s, comp, e)) return SBP_EINVAL;
+    if ((int)s->prb.size() >= sbp::kMaxProbes) return SBP_ECAPACITY;
+    const int idx[3] = {i, j, k};
+    for (int a = 0; a < 3; a++)
+        if (idx[a] < 0 || idx[a] >= e[a]) return SBP_EINVAL;
+    if (s->probe_buf) return SBP_ESTATE;    // add probes before reserving their buffer
+    sbp::Prb q;
+    q.comp = comp; q.i = i; q.j = j; q.k = k;
+    s->prb.push_back(q);
+    if (probe_id) *probe_id = (int)s->prb.size() - 1;
+    return SBP_OK;
+}
+
+int sbp_reserve_probes(sbp_sim *s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    if (s->probe_buf) { cudaFree(s->probe_buf); s->probe_buf = nullptr; }
+    s->probe_cap = 0;
+    const size_t np = std::max<size_t>(1, s->prb.size());
+    if (nsteps > 0) {
+        SBP_CUDA(cudaMalloc(&s->probe_buf, np * nsteps * s->esize));
+        SBP_CUDA(cudaMemsetAsync(s->probe_buf, 0, np * nsteps * s->esize, s->stream));
+        s->probe_cap = nsteps;
+    }
+    s->probe_base = s->step;
+    return SBP_OK;
+}
+
+int sbp_step(sbp_sim *s, int64_t nsteps)
+{
+    if (!s) return SBP_EINVAL;
+    sbp_sim *one[1] = {s};
+    return step_group(one, 1, nsteps);
+}
+
+int sbp_step_group(sbp_sim **sims, int nsims, int64_t nsteps)
+{
+    return step_group(sims, nsims, nsteps);
+}
+
+int sbp_half_step_h(sbp_sim **sims, int nsims)
+{
+    int rc = check_group(sims, nsims);
+    return rc ? rc : half_h(sims, nsims);
+}
+
+int sbp_half_step_e(sbp_sim **sims, int nsims)
+{
+    int rc = check_group(sims, nsims);
+    return rc ? rc : half_e(sims, nsims);
+}
+
+int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples)
+{
+    if (!s || cap < 0 || (!out && cap > 0)) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    const long long rec = std::min<long long>(s->step - s->probe_base, s->probe_cap);
+    if (nsamples) *nsamples = rec;
+    const size_t np = s->prb.size();
+    if (np == 0 || !s->probe_buf || cap == 0) return SBP_OK;
+    std::vector<char> host(np * s->probe_cap * s->esize);
+    SBP_CUDA(cudaMemcpy(host.data(), s->probe_buf, host.size(), cudaMemcpyDeviceToHost));
+    const long long m = std::min<long long>(cap, s->probe_cap);
+    for (size_t q = 0; q < np; q++)
+        for (long long t = 0; t < m; t++) {
+            const size_t src = q * s->probe_cap + t;
+            out[q * cap + t] = s->esize == 8 ? reinterpret_cast<double *>(host.data())[src]
+                                             : (double)reinterpret_cast<float *>(host.data())[src];
+        }
+    return SBP_OK;
+}
+
+int sbp_energy_group(sbp_sim **sims, int nsims, double *W)
+{
+    if (!sims || nsims <= 0 || !W) return SBP_EINVAL;
+    double total = 0.0;
+    for (int q = 0; q < nsims; q++) {
+        sbp_sim *s = sims[q];
+        if (!s) return SBP_EINVAL;
+        cudaSetDevice(s->device);
+        int rc = launch_h_any(s, true, false);
+        if (rc) return rc;
+        rc = finalize_energy(s, s->escalar);
+        if (rc) return rc;
+        double v = 0.0;
+        SBP_CUDA(cudaMemcpyAsync(&v, s->escalar, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        SBP_CUDA(cudaStreamSynchronize(s->stream));
+        total += v;
+    }
+    *W = total;
+    return SBP_OK;
+}
+
+int sbp_energy(sbp_sim *s, double *W)
+{
+    sbp_sim *one[1] = {s};
+    return sbp_energy_group(one, 1, W);
+}
+
+int sbp_energy_series(sbp_sim *s, double *out, int64_t cap, int64_t *count)
+{
+    if (!s || cap < 0 || (!out && cap > 0)) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    if (count) *count = s->eseries_count;
+    if (s->eseries_count == 0) return SBP_OK;
+    std::vector<double> host(s->eseries_count);
+    SBP_CUDA(cudaMemcpy(host.data(), s->eseries, host.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    const long long m = std::min<long long>(cap, s->eseries_count);
+    for (long long t = 0; t < m; t++) out[t] = host[t];
+    for (double v : host)
+        if (!std::isfinite(v) || v > 1.5 * host[0]) return SBP_EUNSTABLE;
+    return SBP_OK;
+}
+
+int sbp_sync(sbp_sim *s)
+{
+    if (!s) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    return SBP_OK;
+}
+
+double sbp_dt(const sbp_sim *s) { return s ? s->dt : 0.0; }
+int64_t sbp_step_index(const sbp_sim *s) { return s ? s->step : -1; }
+
+int sbp_destroy(sbp_sim *s)
+{
+    if (!s) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->stream);
+    for (int f = 0; f < 6; f++) {
+        sbp_sim *nb = s->nbr[f];
+        if (nb && nb != s && s->nbr_face[f] >= 0 && nb->nbr[s->nbr_face[f]] == s) nb->nbr[s->nbr_face[f]] = nullptr;
+    }
+    if (s->probe_buf) cudaFree(s->probe_buf);
+    if (s->eseries) cudaFree(s->eseries);
+    if (s->own_ws && s->workspace) cudaFree(s->workspace);
+    delete s;
+    return SBP_OK;
+}
+
+const char *sbp_strerror(int code)
+{
+    switch (code) {
+    case SBP_OK: return "ok";
+    case SBP_EINVAL: return "invalid argument";
+    case SBP_ENOMEM: return "out of memory";
+    case SBP_ECUDA: return "CUDA runtime error";
+    case SBP_EUNSTABLE: return "energy monitor: growth or non-finite value";
+    case SBP_ETIMEOUT: return "bounded device wait timed out";
+    case SBP_ENOTCONFORMING: return "interface faces do not conform";
+    case SBP_ESTATE: return "call not valid in the current state";
+    case SBP_ECAPACITY: return "buffer too small";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

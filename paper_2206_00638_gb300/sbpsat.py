@@ -1,0 +1,345 @@
+"""Python binding of the C ABI in ``include/sbpsat.h`` (argument marshalling only).
+
+Every step of the leapfrog runs in the CUDA kernels of ``csrc/``; this module
+builds ``libsbpsat.so`` in-tree with nvcc, loads it with ctypes and converts
+numpy arrays / torch tensors to plain pointers.  There is no CPU fallback: if
+the library cannot be built or loaded, every call raises.
+
+PyTorch supplies device memory (the simulation workspace can be a torch
+uint8 tensor, so the caching allocator owns it) and the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_PKG)
+_CSRC = os.path.join(_PKG, "csrc")
+_INC = os.path.join(_ROOT, "include")
+_LIBDIR = os.path.join(_PKG, "_lib")
+LIB_PATH = os.path.join(_LIBDIR, "libsbpsat.so")
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-shared"]
+
+PEC, PMC, ABSORBING, INTERFACE = 0, 1, 2, 3
+FP32, FP64, FP32_FP16STORE = 0, 1, 2
+EX, EY, EZ, HX, HY, HZ = range(6)
+GAUSS, GAUSS_DERIV, MOD_GAUSS = 0, 1, 2
+FLAG_ALLOW_UNSTABLE = 1
+
+ON_PLUS = ((0, 1, 1), (1, 0, 1), (1, 1, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SbpError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = _strerror(code)
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+def _sources():
+    return [os.path.join(_CSRC, f) for f in sorted(os.listdir(_CSRC)) if f.endswith((".cu", ".cuh"))] + \
+        [os.path.join(_INC, "sbpsat.h")]
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a into _lib/libsbpsat.so (in-tree)."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    newest = max(os.path.getmtime(p) for p in _sources())
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["nvcc", *NVCC_FLAGS, "-I" + _INC, "-I" + _CSRC, "-o", tmp, os.path.join(_CSRC, "sbpsat.cu")]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class GridDesc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+        ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+        ("eps_r", C.POINTER(C.c_float)), ("mu_r", C.POINTER(C.c_float)),
+        ("face", C.c_int32 * 6),
+        ("cfl_fraction", C.c_double),
+        ("precision", C.c_int32),
+        ("energy_every", C.c_int32),
+        ("flags", C.c_int32),
+    ]
+
+
+def lib():
+    """Load libsbpsat.so (building it first if needed).  Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = LIB_PATH if os.path.exists(LIB_PATH) else build()
+            L = C.CDLL(path)
+            P, I, D, I64, SZ = C.c_void_p, C.c_int, C.c_double, C.c_int64, C.c_size_t
+            pp = C.POINTER(C.c_void_p)
+            sig = {
+                "sbp_create": (I, [C.POINTER(GridDesc), P, pp]),
+                "sbp_workspace_bytes": (SZ, [C.POINTER(GridDesc)]),
+                "sbp_create_in": (I, [C.POINTER(GridDesc), P, P, SZ, pp]),
+                "sbp_connect": (I, [P, I, P, I]),
+                "sbp_set_field": (I, [P, I, P, I]),
+                "sbp_get_field": (I, [P, I, P, I]),
+                "sbp_add_source": (I, [P, I, I, I, I, I, D, D, D, D]),
+                "sbp_add_probe": (I, [P, I, I, I, I, C.POINTER(C.c_int)]),
+                "sbp_reserve_probes": (I, [P, I64]),
+                "sbp_step": (I, [P, I64]),
+                "sbp_step_group": (I, [pp, I, I64]),
+                "sbp_half_step_h": (I, [pp, I]),
+                "sbp_half_step_e": (I, [pp, I]),
+                "sbp_get_probes": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
+                "sbp_energy": (I, [P, C.POINTER(C.c_double)]),
+                "sbp_energy_group": (I, [pp, I, C.POINTER(C.c_double)]),
+                "sbp_energy_series": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
+                "sbp_sync": (I, [P]),
+                "sbp_dt": (D, [P]),
+                "sbp_step_index": (I64, [P]),
+                "sbp_destroy": (I, [P]),
+                "sbp_strerror": (C.c_char_p, [I]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols() -> Sequence[str]:
+    return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_set_field",
+            "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
+            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_series",
+            "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror"]
+
+
+def _strerror(code: int) -> str:
+    try:
+        return lib().sbp_strerror(code).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "error"
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise SbpError(rc, what)
+    return rc
+
+
+def extents(n, comp):
+    return tuple(int(n[a]) + (1 if ON_PLUS[comp][a] else 2) for a in range(3))
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Sim:
+    """One block of the SBP-SAT FDTD leapfrog on the GPU (wraps ``sbp_sim``).
+
+    n: cells (nx, ny, nz); h: mesh steps (dx, dy, dz) in metres; faces: six
+    face types (x-, x+, y-, y+, z-, z+); eps_r / mu_r: per-cell arrays of shape
+    (nz, ny, nx) or None; cfl: dt as a fraction of the CFL limit.
+    torch_memory=True carves the device arrays from a torch uint8 tensor.
+    """
+
+    def __init__(self, n, h, faces, eps_r=None, mu_r=None, cfl=0.95, precision=FP32,
+                 energy_every=0, flags=0, stream=None, torch_memory=True):
+        L = lib()
+        self.n = tuple(int(v) for v in n)
+        self.h = tuple(float(v) for v in h)
+        self.precision = precision
+        self.dtype = np.float64 if precision == FP64 else np.float32
+        self._keep = []
+        d = GridDesc()
+        d.nx, d.ny, d.nz = self.n
+        d.dx, d.dy, d.dz = self.h
+        ncell = self.n[0] * self.n[1] * self.n[2]
+        for name, arr in (("eps_r", eps_r), ("mu_r", mu_r)):
+            if arr is None:
+                setattr(d, name, None)
+                continue
+            a = np.ascontiguousarray(np.asarray(arr, dtype=np.float32).reshape(-1))
+            if a.size != ncell:
+                raise ValueError(f"{name} must have nx*ny*nz = {ncell} entries")
+            self._keep.append(a)
+            setattr(d, name, a.ctypes.data_as(C.POINTER(C.c_float)))
+        for f in range(6):
+            d.face[f] = int(faces[f])
+        d.cfl_fraction = float(cfl)
+        d.precision = int(precision)
+        d.energy_every = int(energy_every)
+        d.flags = int(flags)
+        self._desc = d
+        self.stream = _stream_ptr(stream)
+        h_out = C.c_void_p()
+        self._ws = None
+        if torch_memory:
+            import torch
+            nbytes = L.sbp_workspace_bytes(C.byref(d))
+            if nbytes == 0:
+                raise SbpError(-1, "sbp_workspace_bytes")
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            _check(L.sbp_create_in(C.byref(d), self.stream, self._ws.data_ptr(), nbytes, C.byref(h_out)),
+                   "sbp_create_in")
+        else:
+            _check(L.sbp_create(C.byref(d), self.stream, C.byref(h_out)), "sbp_create")
+        self._keep.clear()
+        self._h = h_out.value
+        self.nprobes = 0
+
+    # --- lifetime -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sbp_destroy(self._h)
+            self._h = None
+            self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # --- problem statement ----------------------------------------------
+    def shape(self, comp):
+        e = extents(self.n, comp)
+        return (e[2], e[1], e[0])
+
+    def connect(self, face, other: "Sim", other_face):
+        _check(lib().sbp_connect(self._h, int(face), other._h, int(other_face)), "sbp_connect")
+
+    def add_source(self, comp, i, j, k, kind, amp, tw, t0, f=0.0):
+        return _check(lib().sbp_add_source(self._h, comp, i, j, k, kind, amp, tw, t0, f), "sbp_add_source")
+
+    def add_probe(self, comp, i, j, k):
+        pid = C.c_int()
+        _check(lib().sbp_add_probe(self._h, comp, i, j, k, C.byref(pid)), "sbp_add_probe")
+        self.nprobes += 1
+        return pid.value
+
+    def reserve_probes(self, nsteps):
+        _check(lib().sbp_reserve_probes(self._h, int(nsteps)), "sbp_reserve_probes")
+        self.probe_cap = int(nsteps)
+
+    # --- fields ---------------------------------------------------------
+    def set_field(self, comp, arr):
+        """arr: numpy array (host) or CUDA torch tensor of the component's shape."""
+        if hasattr(arr, "data_ptr") and getattr(arr, "is_cuda", False):
+            if tuple(arr.shape) != self.shape(comp) or not arr.is_contiguous():
+                raise ValueError("device tensor must be contiguous with the component's shape")
+            _check(lib().sbp_set_field(self._h, comp, arr.data_ptr(), 1), "sbp_set_field")
+            return
+        a = np.ascontiguousarray(np.asarray(arr, dtype=self.dtype))
+        if a.shape != self.shape(comp):
+            raise ValueError(f"component {comp}: expected {self.shape(comp)}, got {a.shape}")
+        _check(lib().sbp_set_field(self._h, comp, a.ctypes.data, 0), "sbp_set_field")
+
+    def field(self, comp, out=None):
+        """Host copy (numpy) of a component, or into a CUDA torch tensor ``out``."""
+        if out is not None:
+            _check(lib().sbp_get_field(self._h, comp, out.data_ptr(), 1), "sbp_get_field")
+            return out
+        a = np.empty(self.shape(comp), dtype=self.dtype)
+        _check(lib().sbp_get_field(self._h, comp, a.ctypes.data, 0), "sbp_get_field")
+        return a
+
+    # --- time stepping --------------------------------------------------
+    def step(self, nsteps):
+        _check(lib().sbp_step(self._h, int(nsteps)), "sbp_step")
+
+    def sync(self):
+        _check(lib().sbp_sync(self._h), "sbp_sync")
+
+    @property
+    def dt(self):
+        return lib().sbp_dt(self._h)
+
+    @property
+    def step_index(self):
+        return lib().sbp_step_index(self._h)
+
+    def probes(self):
+        cap = getattr(self, "probe_cap", 0)
+        out = np.zeros((max(self.nprobes, 1), max(cap, 1)))
+        ns = C.c_int64()
+        _check(lib().sbp_get_probes(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), max(cap, 1),
+                                    C.byref(ns)), "sbp_get_probes")
+        return out[: self.nprobes, : ns.value]
+
+    def energy(self):
+        w = C.c_double()
+        _check(lib().sbp_energy(self._h, C.byref(w)), "sbp_energy")
+        return w.value
+
+    def energy_series(self):
+        cnt = C.c_int64()
+        _check(lib().sbp_energy_series(self._h, None, 0, C.byref(cnt)), "sbp_energy_series")
+        out = np.zeros(max(cnt.value, 1))
+        rc = lib().sbp_energy_series(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), cnt.value,
+                                     C.byref(cnt))
+        return out[: cnt.value], rc
+
+
+def _handles(sims):
+    return (C.c_void_p * len(sims))(*[s._h for s in sims])
+
+
+def step_group(sims, nsteps):
+    _check(lib().sbp_step_group(_handles(sims), len(sims), int(nsteps)), "sbp_step_group")
+
+
+def half_step_h(sims):
+    _check(lib().sbp_half_step_h(_handles(sims), len(sims)), "sbp_half_step_h")
+
+
+def half_step_e(sims):
+    _check(lib().sbp_half_step_e(_handles(sims), len(sims)), "sbp_half_step_e")
+
+
+def energy_group(sims):
+    w = C.c_double()
+    _check(lib().sbp_energy_group(_handles(sims), len(sims), C.byref(w)), "sbp_energy_group")
+    return w.value
+
+
+def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_every=0):
+    """Create the GPU blocks of a workloads.Workload (fields, sources, probes, links)."""
+    sims = []
+    for b in w.blocks:
+        s = Sim(b.n, b.h, b.faces, eps_r=b.eps_r, mu_r=b.mu_r, cfl=w.cfl, precision=precision,
+                stream=stream, torch_memory=torch_memory, energy_every=energy_every)
+        if b.fields is not None:
+            for c in range(6):
+                s.set_field(c, b.fields[c])
+        for src in b.sources:
+            s.add_source(src.comp, src.i, src.j, src.k, src.kind, src.amp, src.tw, src.t0, src.f)
+        for p in b.probes:
+            s.add_probe(p.comp, p.i, p.j, p.k)
+        sims.append(s)
+    for a, fa, b, fb in w.links:
+        sims[a].connect(fa, sims[b], fb)
+    return sims

@@ -183,3 +183,41 @@ def mixed_faces(N: int = 512, seed: int = 5, steps: int = 1000, h: float = 1e-3)
                     eps_r=eps, sources=[Source(EY, -1, -1, N // 16, GAUSS, 1.0, tw, tw)],
                     probes=[Probe(EY, N // 2, N // 2, N // 2)])
     return Workload(f"mixed_faces_{N}^3", [blk], [], 0.95, steps)
+
+
+def random_box(n, h=(1e-3, 1e-3, 1e-3), faces=(PEC,) * 6, seed: int = 0, eps_range=(1.0, 4.0),
+               mu_range=None, cfl: float = 0.95, steps: int = 100, nprobes: int = 12,
+               sources: bool = True) -> Workload:
+    """Parity workload: seeded per-cell eps_r ~ U[eps_range] (and mu_r if given), random
+    initial fields on every node (E ~ U(-1, 1) V/m, H ~ U(-1, 1)/377 A/m), a
+    Gaussian-derivative point source on Ez, a Gaussian sheet on Ex, and probes of
+    all six components at seeded nodes (boundary nodes included)."""
+    n = tuple(int(v) for v in n)
+    rng = np.random.default_rng(seed)
+    eps = rng.uniform(*eps_range, size=(n[2], n[1], n[0])).astype(np.float32)
+    mu = None if mu_range is None else rng.uniform(*mu_range, size=(n[2], n[1], n[0])).astype(np.float32)
+    fields = [rng.uniform(-1.0, 1.0, size=field_shape(n, c)) * (1.0 if c < 3 else 1.0 / 377.0)
+              for c in range(6)]
+    srcs = []
+    if sources:
+        tw = gaussian_deriv_tw(20e9)
+        ez = extents(n, EZ)
+        srcs.append(Source(EZ, int(rng.integers(0, ez[0])), int(rng.integers(0, ez[1])),
+                           int(rng.integers(0, ez[2])), GAUSS_DERIV, 2.0, tw, tw))
+        srcs.append(Source(EX, -1, -1, int(rng.integers(0, extents(n, EX)[2])), GAUSS, 1.0, 2 * tw, 2 * tw))
+    probes = []
+    for p in range(nprobes):
+        comp = p % 6
+        e = extents(n, comp)
+        probes.append(Probe(comp, *[int(rng.integers(0, e[a])) for a in range(3)]))
+    blk = BlockSpec(n=n, h=tuple(h), faces=tuple(faces), eps_r=eps, mu_r=mu, fields=fields,
+                    sources=srcs, probes=probes)
+    return Workload(f"random_box_{n[0]}x{n[1]}x{n[2]}", [blk], [], cfl, steps)
+
+
+def coupled_boxes(nA, nB, axis: int, h=(1e-3, 1e-3, 1e-3), facesA=(PEC,) * 6, facesB=(PEC,) * 6,
+                  seed: int = 0, cfl: float = 0.95, steps: int = 100) -> Workload:
+    """Two random boxes joined high face of A to low face of B along axis (conforming)."""
+    wa = random_box(nA, h, facesA, seed=seed, cfl=cfl, steps=steps)
+    wb = random_box(nB, h, facesB, seed=seed + 1, cfl=cfl, steps=steps, sources=False)
+    return Workload(f"coupled_{axis}", wa.blocks + wb.blocks, [(0, 2 * axis + 1, 1, 2 * axis)], cfl, steps)

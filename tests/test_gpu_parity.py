@@ -1,0 +1,182 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP32 path <= 1e-5 relative L2 per field after the run (the
+accuracy bound stated for the FP32 fused kernels), FP64 path <= 1e-11
+(same arithmetic up to rounding order and FMA contraction).
+"""
+import numpy as np
+import pytest
+
+from paper_2206_00638_gb300 import workloads as wl
+from tests import parity
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2206_00638_gb300 import sbpsat  # noqa: E402
+
+TOL = {sbpsat.FP32: 1e-5, sbpsat.FP64: 1e-11}
+PTOL = {sbpsat.FP32: 5e-5, sbpsat.FP64: 1e-10}
+P, M, A = wl.PEC, wl.PMC, wl.ABSORBING
+
+
+def _run_and_compare(w, steps, precision):
+    sims = parity.gpu_run(w, steps, precision)
+    blocks = parity.oracle_run(w, steps, sims[0].dt)
+    errs = parity.compare(sims, blocks)
+    perr = parity.probe_error(sims, blocks)
+    for s in sims:
+        s.close()
+    return errs, perr
+
+
+@pytest.mark.parametrize("precision", [sbpsat.FP64, sbpsat.FP32])
+def test_cavity_workload(precision):
+    """PEC cavity 20x16x12 (0.9 CFL, 500 steps): GPU fields and the Ez probe match the oracle."""
+    w = wl.cavity()
+    errs, perr = _run_and_compare(w, w.steps, precision)
+    assert max(errs[0]) < TOL[precision], errs
+    assert perr < PTOL[precision]
+
+
+FACES = [
+    (P, P, P, P, P, P),
+    (M, M, M, M, M, M),
+    (P, M, M, P, A, P),
+    (A, A, A, A, A, A),
+    (M, A, P, A, A, M),
+]
+
+
+@pytest.mark.parametrize("faces", FACES)
+@pytest.mark.parametrize("precision", [sbpsat.FP64, sbpsat.FP32])
+def test_random_box_all_faces(faces, precision):
+    """Ragged box (several tiles, ragged tails in x, y, z) with random eps_r, random fields,
+    point + sheet sources and probes of every component, every face type."""
+    w = wl.random_box((70, 43, 37), faces=faces, seed=11, steps=150)
+    errs, perr = _run_and_compare(w, w.steps, precision)
+    assert max(errs[0]) < TOL[precision], errs
+    assert perr < PTOL[precision]
+
+
+@pytest.mark.parametrize("n", [(4, 4, 4), (5, 4, 6), (4, 9, 4), (33, 8, 5)])
+@pytest.mark.parametrize("precision", [sbpsat.FP64, sbpsat.FP32])
+def test_minimum_and_thin_grids(n, precision):
+    """Smallest legal grids (4 cells: closures meet) and thin slabs."""
+    w = wl.random_box(n, faces=(P, A, M, P, A, M), seed=5, steps=60)
+    errs, perr = _run_and_compare(w, w.steps, precision)
+    assert max(errs[0]) < TOL[precision], errs
+
+
+@pytest.mark.parametrize("precision", [sbpsat.FP64, sbpsat.FP32])
+def test_variable_mu(precision):
+    w = wl.random_box((36, 29, 21), faces=(P, M, A, P, M, A), seed=3, steps=100, mu_range=(1.0, 3.0))
+    errs, perr = _run_and_compare(w, w.steps, precision)
+    assert max(errs[0]) < TOL[precision], errs
+    assert perr < PTOL[precision]
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("precision", [sbpsat.FP64, sbpsat.FP32])
+def test_interface_two_blocks(axis, precision):
+    """Conforming interface SAT between two blocks (different normal extents and pitches)."""
+    nA = [37, 26, 19]
+    nB = [37, 26, 19]
+    nB[axis] = 23 if axis else 61
+    w = wl.coupled_boxes(nA, nB, axis, facesA=(A, P, M, A, P, A), facesB=(P, A, A, M, A, P), seed=7, steps=120)
+    errs, perr = _run_and_compare(w, w.steps, precision)
+    for e in errs:
+        assert max(e) < TOL[precision], errs
+    assert perr < PTOL[precision]
+
+
+@pytest.mark.parametrize("precision", [sbpsat.FP64, sbpsat.FP32])
+def test_periodic_self_link(precision):
+    """A block joined to itself across y (zero-phase periodic SAT)."""
+    w = wl.random_box((30, 22, 17), faces=(P, P, M, M, A, A), seed=9, steps=120)
+    w.links = [(0, 3, 0, 2)]
+    errs, perr = _run_and_compare(w, w.steps, precision)
+    assert max(errs[0]) < TOL[precision], errs
+
+
+def test_energy_fp64_conserved_and_matches_oracle():
+    """GPU FP64 energy (Eq. (16), leapfrog form): equals the oracle's and is conserved."""
+    import oracle
+    w = wl.random_box((26, 19, 23), faces=(P, M, P, M, M, P), seed=2, steps=200, sources=False)
+    sim = sbpsat.from_workload(w, precision=sbpsat.FP64)[0]
+    blk = parity.oracle_blocks(w, sim.dt)[0]
+    W0 = sim.energy()
+    assert W0 == pytest.approx(oracle.energy([blk]), rel=1e-12)
+    sim.step(200)
+    W1 = sim.energy()
+    assert abs(W1 - W0) / W0 < 1e-12
+    sim.close()
+
+
+def test_energy_series_fp32_monitor():
+    """Energy monitor every 10 steps (FP64 reduction of FP32 fields): flat to FP32 round-off."""
+    w = wl.random_box((40, 33, 29), faces=(P, P, M, M, P, M), seed=4, steps=300, sources=False)
+    sim = sbpsat.from_workload(w, precision=sbpsat.FP32, energy_every=10)[0]
+    sim.step(300)
+    series, rc = sim.energy_series()
+    assert rc == 0 and len(series) == 30
+    assert np.max(np.abs(series - series[0])) / series[0] < 1e-5
+    sim.close()
+
+
+def test_unstable_cfl_detected():
+    """cfl = 1.2 (allowed by flag) grows without bound: the monitor reports SBP_EUNSTABLE."""
+    w = wl.random_box((20, 18, 16), faces=(P,) * 6, seed=1, steps=600, sources=False)
+    b = w.blocks[0]
+    sim = sbpsat.Sim(b.n, b.h, b.faces, eps_r=b.eps_r, cfl=1.2, flags=sbpsat.FLAG_ALLOW_UNSTABLE,
+                     energy_every=20)
+    for c in range(6):
+        sim.set_field(c, b.fields[c])
+    sim.step(600)
+    series, rc = sim.energy_series()
+    assert rc == -4
+    sim.close()
+
+
+def test_deterministic_and_own_memory():
+    """Two runs (torch workspace vs library-owned memory) are bitwise identical."""
+    w = wl.random_box((45, 38, 31), faces=(A, P, M, A, P, M), seed=8, steps=80)
+    s1 = parity.gpu_run(w, 80, sbpsat.FP32)[0]
+    s2 = parity.gpu_run(w, 80, sbpsat.FP32, torch_memory=False)[0]
+    for c in range(6):
+        assert np.array_equal(s1.field(c), s2.field(c))
+    assert np.array_equal(s1.probes(), s2.probes())
+
+
+def test_device_field_roundtrip():
+    w = wl.random_box((12, 10, 9), seed=1, sources=False)
+    sim = sbpsat.from_workload(w)[0]
+    for c in range(6):
+        t = torch.randn(sim.shape(c), device="cuda", dtype=torch.float32)
+        sim.set_field(c, t)
+        out = torch.empty_like(t)
+        sim.field(c, out=out)
+        torch.cuda.synchronize()
+        assert torch.equal(t, out)
+        assert np.array_equal(sim.field(c), t.cpu().numpy())
+    sim.close()
+
+
+def test_fp32_accuracy_2000_steps():
+    """Dielectric-cube workload scaled to 64^3 at the full 2000 steps: FP32 within 1e-5."""
+    w = wl.dielectric(N=64, steps=2000)
+    errs, perr = _run_and_compare(w, w.steps, sbpsat.FP32)
+    assert max(errs[0]) < 1e-5, errs
+    assert perr < 1e-4
+
+
+def test_full_size_dielectric_256():
+    """Full-size 256^3 dielectric workload in the benchmark's launch configuration:
+    element-wise parity for the first 40 steps (every field), FP32."""
+    w = wl.dielectric(N=256, steps=40)
+    errs, perr = _run_and_compare(w, w.steps, sbpsat.FP32)
+    assert max(errs[0]) < 1e-5, errs
+    assert perr < 1e-4
