@@ -169,6 +169,13 @@ __device__ __forceinline__ double norm_weight(bool plus, int r, int n)
 
 __device__ __forceinline__ int extent(const int n[3], int c, int a) { return n[a] + (on_plus(c, a) ? 1 : 2); }
 
+// (m[o] + m[o+a]) + (m[o+b] + m[o+a+b])
+template <typename S>
+__device__ __forceinline__ S pair_sum(const float *__restrict__ m, long long o, long long a, long long b)
+{
+    return (S(__ldg(m + o)) + S(__ldg(m + o + a))) + (S(__ldg(m + o + b)) + S(__ldg(m + o + a + b)));
+}
+
 // Sum of the ghost-padded cell values around a node of component c: the
 // closed-box cell set of the node, always 2x2 (E) or 2x1 (H) entries after
 // ghost padding (duplicates stand for clipped cells, so the mean is the mean
@@ -178,15 +185,14 @@ __device__ __forceinline__ S cell_sum(const float *__restrict__ m, long long o, 
 {
     // ghost-padded index of the node's first cell is the node index itself;
     // a plus-grid axis spans two cells (offset 0 and +1), a minus-grid axis one.
+    // Summed pairwise, (a + b) + (c + d): exact whenever the cells agree, and
+    // the same order in the fast and the general path.
     constexpr bool px = on_plus(C, 0), py = on_plus(C, 1), pz = on_plus(C, 2);
-    S s = S(__ldg(m + o));
-    if (px) s += S(__ldg(m + o + 1));
-    if (py) s += S(__ldg(m + o + sy));
-    if (pz) s += S(__ldg(m + o + sz));
-    if (px && py) s += S(__ldg(m + o + 1 + sy));
-    if (px && pz) s += S(__ldg(m + o + 1 + sz));
-    if (py && pz) s += S(__ldg(m + o + sy + sz));
-    return s;
+    if (px && py) return pair_sum<S>(m, o, 1, sy);
+    if (px && pz) return pair_sum<S>(m, o, 1, sz);
+    if (py && pz) return pair_sum<S>(m, o, sy, sz);
+    const long long d = px ? 1 : py ? sy : sz;
+    return S(__ldg(m + o)) + S(__ldg(m + o + d));
 }
 // number of entries summed by cell_sum<C>
 __host__ __device__ constexpr int cell_count(int c)
@@ -545,12 +551,14 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T> p)
             ax.add(Ay, hz_jp - hzc); ax.add(Az, hyn - hyc, T(-1));
             ay.add(Az, hxn - hxc);   ay.add(Ax, hz_ip - hzc, T(-1));
             az.add(Ax, hy_ip - hyc); az.add(Ay, hx_jp - hxc, T(-1));
-            const float sx = (f00 + f01) + (e00 + e01);
-            const float sy = (f00 + f10) + (e00 + e10);
-            const float sz = (f00 + f10) + (f01 + f11);
-            Ex[o] = Ex[o] + scaled_increment(ax, T(sx));
-            Ey[o] = Ey[o] + scaled_increment(ay, T(sy));
-            Ez[o] = Ez[o] + scaled_increment(az, T(sz));
+            // node sums in the association of cell_sum: Ex (m, +sy, +sz, +sy+sz),
+            // Ey (m, +1, +sz, +1+sz), Ez (m, +1, +sy, +1+sy)
+            const T sx = (T(f00) + T(f01)) + (T(e00) + T(e01));
+            const T sy = (T(f00) + T(f10)) + (T(e00) + T(e10));
+            const T sz = (T(f00) + T(f10)) + (T(f01) + T(f11));
+            Ex[o] = Ex[o] + scaled_increment(ax, sx);
+            Ey[o] = Ey[o] + scaled_increment(ay, sy);
+            Ez[o] = Ez[o] + scaled_increment(az, sz);
         } else {
             const int idx[3] = {i, j, k};
             if (i <= nx + 1 && j <= ny && k <= nz) {          // Ex (x-, y+, z+)

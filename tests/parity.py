@@ -16,6 +16,7 @@ def oracle_blocks(w, dt):
             blk.add_source(s.comp, s.i, s.j, s.k, s.kind, s.amp, s.tw, s.t0, s.f)
         for p in b.probes:
             blk.add_probe(p.comp, p.i, p.j, p.k)
+        blk.probe_specs = list(b.probes)
         blocks.append(blk)
     for a, fa, b, fb in w.links:
         oracle.connect(blocks[a], fa, blocks[b], fb)
@@ -47,20 +48,45 @@ def rel_l2(a, b):
 
 
 def compare(sims, blocks):
-    """Per-block, per-component relative L2 error, and max relative probe error."""
+    """Per block: relative L2 error of the E field and of the H field (all three components
+    together), the reading of "relative L2 error per field" used throughout."""
     errs = []
     for s, b in zip(sims, blocks):
-        errs.append([rel_l2(s.field(c).astype(np.float64), b.field(c)) for c in range(6)])
+        row = []
+        for comps in ((0, 1, 2), (3, 4, 5)):
+            num = sum(np.sum((s.field(c).astype(np.float64) - b.field(c)) ** 2) for c in comps)
+            den = sum(np.sum(b.field(c) ** 2) for c in comps)
+            row.append(float(np.sqrt(num / den)) if den > 0 else float(np.sqrt(num)))
+        errs.append(row)
     return errs
 
 
+def component_errors(sims, blocks):
+    """Per block, per component: ||gpu - ref|| / ||ref field|| (E or H norm)."""
+    out = []
+    for s, b in zip(sims, blocks):
+        ref = [b.field(c) for c in range(6)]
+        nE = np.sqrt(sum(np.sum(r ** 2) for r in ref[:3]))
+        nH = np.sqrt(sum(np.sum(r ** 2) for r in ref[3:]))
+        out.append([float(np.linalg.norm(s.field(c).astype(np.float64) - ref[c]) / (nE if c < 3 else nH))
+                    for c in range(6)])
+    return out
+
+
 def probe_error(sims, blocks):
+    """Max probe error, each probe scaled by the peak of all probes of its field (E or H)."""
     worst = 0.0
     for s, b in zip(sims, blocks):
         if b.nprobes == 0:
             continue
-        g, r = s.probes(), b.probes()
-        scale = np.max(np.abs(r), axis=1, keepdims=True)
-        scale[scale == 0] = 1.0
-        worst = max(worst, float(np.max(np.abs(g - r[:, : g.shape[1]]) / scale)))
+        g, r = s.probes(), b.probes()[:, : s.probes().shape[1]]
+        comps = np.array([p.comp for p in b.probe_specs]) if hasattr(b, "probe_specs") else None
+        peak = np.max(np.abs(r), axis=1)
+        if comps is not None:
+            for isH in (False, True):
+                sel = (comps >= 3) == isH
+                if sel.any():
+                    peak[sel] = max(peak[sel].max(), 1e-300)
+        peak[peak == 0] = 1.0
+        worst = max(worst, float(np.max(np.abs(g - r) / peak[:, None])))
     return worst

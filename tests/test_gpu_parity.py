@@ -1,8 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances: FP32 path <= 1e-5 relative L2 per field after the run (the
-accuracy bound stated for the FP32 fused kernels), FP64 path <= 1e-11
-(same arithmetic up to rounding order and FMA contraction).
+Tolerances: FP32 path <= 1e-5 relative L2 error per field (E and H, each over
+its three components) after the run, the accuracy bound stated for the FP32
+fused kernels; FP64 path <= 1e-11 (same arithmetic up to rounding order and
+FMA contraction).  Probe series: max error relative to the probe's peak.
 """
 import numpy as np
 import pytest
@@ -131,7 +132,7 @@ def test_unstable_cfl_detected():
     """cfl = 1.2 (allowed by flag) grows without bound: the monitor reports SBP_EUNSTABLE."""
     w = wl.random_box((20, 18, 16), faces=(P,) * 6, seed=1, steps=600, sources=False)
     b = w.blocks[0]
-    sim = sbpsat.Sim(b.n, b.h, b.faces, eps_r=b.eps_r, cfl=1.2, flags=sbpsat.FLAG_ALLOW_UNSTABLE,
+    sim = sbpsat.Sim(b.n, b.h, b.faces, eps_r=None, cfl=1.2, flags=sbpsat.FLAG_ALLOW_UNSTABLE,
                      energy_every=20)
     for c in range(6):
         sim.set_field(c, b.fields[c])
