@@ -1,0 +1,401 @@
+// One-pass leapfrog step for the deep interior, fed by TMA (sm_103a).
+//
+// fused_interior computes, in a single sweep over z,
+//   H^{n+1/2} = H^{n-1/2} + dt/mu  (D- E^n)          on I_H = [3, n-2]^3
+//   E^{n+1}   = E^n      + dt/eps (D+ H^{n+1/2} - J) on I_E = [3, n-3]^3
+// where every difference is the two-point interior row of the Appendix
+// operators and no SAT applies (Eqs. (7)-(12), Algs. 1-2 interior loops).
+// Reading E^n, H^{n-1/2} and eps_r once and writing H^{n+1/2}, E^{n+1} once
+// moves 13 words per cell instead of the 18 + 1 of two separate half-step
+// kernels.  Because H^{n+1/2} of a neighbouring tile is needed before that
+// tile has written it, the new fields go to a second buffer set (ping-pong)
+// and each CTA recomputes the one-node H halo it needs.
+//
+// CTA = 8 warps, tile of H columns x0..x0+63 and rows y0..y0+7 (warp = row,
+// lane = columns x0+L and x0+32+L); E is produced for the inner 63 x 7.  A
+// 4-stage pipeline of 3D TMA tensor copies (one box per field per z-plane,
+// completion on an mbarrier) keeps ~48 KB per CTA in flight; H^{n+1/2} of
+// the current and next plane is exchanged through shared memory.
+//
+// band_h / band_e evaluate the remaining nodes (the three boundary layers of
+// each axis, closure rows and SAT penalties) with the general-path code of
+// kernels.cuh, reading the old set and writing the new one.
+#pragma once
+#include <cuda.h>
+
+#include "kernels.cuh"
+
+namespace sbp {
+
+constexpr int kFTX = 64;                 // H footprint width
+constexpr int kFTY = 8;                  // H footprint rows (= warps)
+constexpr int kFBX = kFTX + 4;           // TMA box width: x0-1 .. x0+63 from a 4-aligned start
+constexpr int kStages = 4;
+constexpr int kERows = kFTY + 1;         // E rows y0-1 .. y0+7
+constexpr int kHRows = kFTY;             // H / eps rows y0 .. y0+7
+constexpr int kEField = 640;             // floats per E box slot (9*68 = 612, 128-byte rounded)
+constexpr int kHField = 576;             // floats per H / eps box slot (8*68 = 544, rounded)
+constexpr int kStageFloats = 3 * kEField + 4 * kHField;
+constexpr int kStageBytesTx = (3 * kERows * kFBX + 4 * kHRows * kFBX) * 4;   // bytes the TMA delivers
+constexpr int kHbufFloats = 2 * 3 * kFTY * kFTX;
+constexpr int kFusedSmem = (kStages * kStageFloats + kHbufFloats) * 4 + kStages * 8;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+struct FusedParams {
+    float *out[6];                       // new set: element (i,j,k) at k*sz + j*sy + i
+    int n[3];
+    long long sy, sz;
+    Coef<float> B[3], A[3], AJ;
+    double dt;
+    int nsrc, nprb;
+    Src src[kMaxSources];
+    Prb prb[kMaxProbes];
+    float *probe_buf;
+    long long probe_cap, probe_slot, step;
+    int kchunk;
+    int *error_flag;                     // set to 1 when a pipeline wait gives up
+};
+
+// --- mbarrier / TMA helpers (inline PTX) ----------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within kWaitLimit polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+{
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+struct FusedMaps {
+    CUtensorMap e[3], h[3], eps;
+};
+
+__device__ __forceinline__ void issue_plane(const FusedMaps &m, float *stage, uint64_t *bar, int xb, int y0, int plane)
+{
+    mbar_expect_tx(bar, kStageBytesTx);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) tma_load_3d(stage + f * kEField, &m.e[f], xb, y0 - 1, plane, bar);
+#pragma unroll
+    for (int f = 0; f < 3; ++f) tma_load_3d(stage + 3 * kEField + f * kHField, &m.h[f], xb, y0, plane, bar);
+    tma_load_3d(stage + 3 * kEField + 3 * kHField, &m.eps, xb, y0, plane, bar);
+}
+
+template <bool SRC>
+__global__ void __launch_bounds__(kFTY * 32, 2) fused_interior(const __grid_constant__ FusedMaps maps, const FusedParams p)
+{
+    extern __shared__ __align__(128) float smem[];
+    float *hbuf = smem + kStages * kStageFloats;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(hbuf + kHbufFloats);
+
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    const int x0 = 3 + blockIdx.x * (kFTX - 1);
+    const int y0 = 3 + blockIdx.y * (kFTY - 1);
+    const int k0 = 3 + blockIdx.z * p.kchunk;
+    const int k1 = min(k0 + p.kchunk, nz - 2);       // E planes [k0, k1); H planes [k0, k1]
+    const int xb = (x0 - 1) & ~3;
+    const int cx0 = x0 - xb;                          // smem column of x0, in 1..4
+    const int nplanes = k1 - k0 + 2;                  // planes k0-1 .. k1 are loaded
+    const int j = y0 + w;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int issued = 0;                                   // planes issued (thread 0's count)
+    if (threadIdx.x == 0)
+        for (; issued < kStages && issued < nplanes; ++issued)
+            issue_plane(maps, smem + issued * kStageFloats, &bar[issued], xb, y0, k0 - 1 + issued);
+
+    // per-thread probe / source masks for the two columns
+    unsigned long long pmask[2] = {0ull, 0ull};
+    unsigned smask[2] = {0u, 0u};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = x0 + lane + 32 * h;
+        for (int q = 0; q < p.nprb; ++q)
+            if (p.prb[q].i == i && p.prb[q].j == j) pmask[h] |= 1ull << q;
+        if (SRC)
+            for (int q = 0; q < p.nsrc; ++q)
+                if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) smask[h] |= 1u << q;
+    }
+    const bool rowE = w < kFTY - 1 && j <= ny - 3;
+    const bool rowH = j <= ny - 2 && (w < kFTY - 1 || j == ny - 2);
+    const Coef<float> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
+    const Coef<float> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
+    const double t_half = ((double)p.step + 0.5) * p.dt;
+
+    bool ok = true;
+    bool aborted = false;
+    int waited = 0;                                   // load index of the next plane to wait for
+    if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0); waited = 1; }
+    for (int q = k0; q <= k1; ++q) {
+        const int iq = q - k0 + 1;                   // load index of plane q
+        const int sq = iq % kStages, sm = (iq - 1) % kStages;
+        if (ok) ok = mbar_wait_bounded(&bar[sq], (iq / kStages) & 1);
+        waited = iq + 1;
+        const float *Sq = smem + sq * kStageFloats;   // plane q
+        const float *Sm = smem + sm * kStageFloats;   // plane q-1
+        float *Hq = hbuf + (q & 1) * (3 * kFTY * kFTX);
+        const float *Hp = hbuf + ((q - 1) & 1) * (3 * kFTY * kFTX);
+
+        // ---- H^{n+1/2} on plane q ------------------------------------------
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = lane + 32 * h;
+            const int cc = cx0 + c;
+            const int re = (w + 1) * kFBX + cc;           // E slot row of j
+            const int rh = w * kFBX + cc;                 // H slot row of j
+            const float exq = Sq[0 * kEField + re], exm = Sm[0 * kEField + re], ex_jm = Sq[0 * kEField + re - kFBX];
+            const float eyq = Sq[1 * kEField + re], eym = Sm[1 * kEField + re], ey_im = Sq[1 * kEField + re - 1];
+            const float ezq = Sq[2 * kEField + re], ez_im = Sq[2 * kEField + re - 1], ez_jm = Sq[2 * kEField + re - kFBX];
+            Acc<float> ax, ay, az;
+            ax.add(Bz, eyq - eym); ax.add(By, ezq - ez_jm, -1.f);
+            ay.add(Bx, ezq - ez_im); ay.add(Bz, exq - exm, -1.f);
+            az.add(By, exq - ex_jm); az.add(Bx, eyq - ey_im, -1.f);
+            const float hx = Sq[3 * kEField + 0 * kHField + rh] + plain_increment(ax);
+            const float hy = Sq[3 * kEField + 1 * kHField + rh] + plain_increment(ay);
+            const float hz = Sq[3 * kEField + 2 * kHField + rh] + plain_increment(az);
+            Hq[(0 * kFTY + w) * kFTX + c] = hx;
+            Hq[(1 * kFTY + w) * kFTX + c] = hy;
+            Hq[(2 * kFTY + w) * kFTX + c] = hz;
+            const int i = x0 + c;
+            if (rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2) && (q < k1 || q == nz - 2)) {
+                const long long o = (long long)q * p.sz + (long long)j * p.sy + i;
+                p.out[3][o] = hx;
+                p.out[4][o] = hy;
+                p.out[5][o] = hz;
+                if (pmask[h]) {
+                    unsigned long long m = pmask[h];
+                    while (m) {
+                        const int b = __ffsll(m) - 1;
+                        m &= m - 1;
+                        const Prb &P = p.prb[b];
+                        if (P.k == q && P.comp >= 3 && p.probe_slot < p.probe_cap)
+                            p.probe_buf[(long long)b * p.probe_cap + p.probe_slot] = P.comp == 3 ? hx : P.comp == 4 ? hy : hz;
+                    }
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) { aborted = true; break; }
+
+        // ---- E^{n+1} on plane q-1 --------------------------------------------
+        if (q > k0 && rowE) {
+            const int pl = q - 1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = lane + 32 * h;
+                const int i = x0 + c;
+                if (c >= kFTX - 1 || i > nx - 3) continue;
+                const int cc = cx0 + c;
+                const float hx = Hp[(0 * kFTY + w) * kFTX + c], hx_jp = Hp[(0 * kFTY + w + 1) * kFTX + c];
+                const float hy = Hp[(1 * kFTY + w) * kFTX + c], hy_ip = Hp[(1 * kFTY + w) * kFTX + c + 1];
+                const float hz = Hp[(2 * kFTY + w) * kFTX + c], hz_ip = Hp[(2 * kFTY + w) * kFTX + c + 1];
+                const float hz_jp = Hp[(2 * kFTY + w + 1) * kFTX + c];
+                const float hxn = Hq[(0 * kFTY + w) * kFTX + c], hyn = Hq[(1 * kFTY + w) * kFTX + c];
+                Acc<float> ax, ay, az;
+                ax.add(Ay, hz_jp - hz); ax.add(Az, hyn - hy, -1.f);
+                ay.add(Az, hxn - hx);   ay.add(Ax, hz_ip - hz, -1.f);
+                az.add(Ax, hy_ip - hy); az.add(Ay, hx_jp - hx, -1.f);
+                // eps cells: slot rows of j and j+1 on planes pl (Sm) and q (Sq)
+                const float *ep = Sm + 3 * kEField + 3 * kHField, *eq = Sq + 3 * kEField + 3 * kHField;
+                const int r0 = w * kFBX + cc, r1 = r0 + kFBX;
+                const float sx = (ep[r0] + ep[r1]) + (eq[r0] + eq[r1]);
+                const float sy = (ep[r0] + ep[r0 + 1]) + (eq[r0] + eq[r0 + 1]);
+                const float sz = (ep[r0] + ep[r0 + 1]) + (ep[r1] + ep[r1 + 1]);
+                if (SRC && smask[h]) {
+                    unsigned m = smask[h];
+                    while (m) {
+                        const int b = __ffs(m) - 1;
+                        m &= m - 1;
+                        const Src &S = p.src[b];
+                        if (S.k < 0 || S.k == pl) {
+                            const float J = (float)(S.amp * waveform(S.wf, t_half, S.tw, S.t0, S.f));
+                            if (S.comp == 0) ax.add(p.AJ, J, -1.f);
+                            else if (S.comp == 1) ay.add(p.AJ, J, -1.f);
+                            else az.add(p.AJ, J, -1.f);
+                        }
+                    }
+                }
+                const int re = (w + 1) * kFBX + cc;
+                const float ex = Sm[0 * kEField + re] + scaled_increment(ax, sx);
+                const float ey = Sm[1 * kEField + re] + scaled_increment(ay, sy);
+                const float ez = Sm[2 * kEField + re] + scaled_increment(az, sz);
+                const long long o = (long long)pl * p.sz + (long long)j * p.sy + i;
+                p.out[0][o] = ex;
+                p.out[1][o] = ey;
+                p.out[2][o] = ez;
+                if (pmask[h]) {
+                    unsigned long long m = pmask[h];
+                    while (m) {
+                        const int b = __ffsll(m) - 1;
+                        m &= m - 1;
+                        const Prb &P = p.prb[b];
+                        if (P.k == pl && P.comp < 3 && p.probe_slot < p.probe_cap)
+                            p.probe_buf[(long long)b * p.probe_cap + p.probe_slot] = P.comp == 0 ? ex : P.comp == 1 ? ey : ez;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // plane q-1 is consumed: refill its stage with plane q-1+kStages
+        if (threadIdx.x == 0) {
+            const int nxt = q - 1 + kStages;
+            if (nxt <= k1) {
+                issue_plane(maps, smem + sm * kStageFloats, &bar[sm], xb, y0, nxt);
+                ++issued;
+            }
+        }
+    }
+    if (aborted && threadIdx.x == 0) {
+        // a pipeline wait gave up: flag it, then wait (bounded) for every copy
+        // still in flight so that none lands in shared memory after exit
+        atomicExch(p.error_flag, 1);
+        for (int L = waited > 0 ? waited - 1 : 0; L < issued; ++L)
+            (void)mbar_wait_bounded(&bar[L % kStages], (L / kStages) & 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Band kernels: every node outside the interior box [lo, hi_a] of its phase.
+// The band is split into disjoint slabs: full z-planes below lo / above hi,
+// then full y-rows of the remaining planes, then the x-ends of what is left.
+// ---------------------------------------------------------------------------
+struct Band {
+    int lo;
+    int hi[3];               // interior box upper bound per axis (inclusive)
+    long long nz_slab, ny_slab, nx_slab;   // node counts of the three slabs
+};
+
+__device__ __forceinline__ void band_node(const Band &b, const int n[3], long long t, int &i, int &j, int &k)
+{
+    const int ex = n[0] + 2, ey = n[1] + 2;
+    const int lo = b.lo;
+    if (t < b.nz_slab) {
+        const long long plane = t / ((long long)ex * ey);
+        const long long r = t % ((long long)ex * ey);
+        k = plane < lo ? (int)plane : b.hi[2] + 1 + (int)(plane - lo);
+        j = (int)(r / ex);
+        i = (int)(r % ex);
+        return;
+    }
+    t -= b.nz_slab;
+    const int ylo = lo, yhi_cnt = (n[1] + 1) - b.hi[1];   // rows above hi: hi+1 .. n+1
+    const int nyr = ylo + yhi_cnt;
+    if (t < b.ny_slab) {
+        const long long per_k = (long long)nyr * ex;
+        k = lo + (int)(t / per_k);
+        const long long r = t % per_k;
+        const int yr = (int)(r / ex);
+        j = yr < ylo ? yr : b.hi[1] + 1 + (yr - ylo);
+        i = (int)(r % ex);
+        return;
+    }
+    t -= b.ny_slab;
+    const int xhi_cnt = (n[0] + 1) - b.hi[0];
+    const int nxr = lo + xhi_cnt;
+    const int nyin = b.hi[1] - lo + 1;
+    const long long per_k = (long long)nyin * nxr;
+    k = lo + (int)(t / per_k);
+    const long long r = t % per_k;
+    j = lo + (int)(r / nxr);
+    const int xr = (int)(r % nxr);
+    i = xr < lo ? xr : b.hi[0] + 1 + (xr - lo);
+}
+
+// H^{n+1/2} on the band: p.F = {E^n (old), H^{n-1/2} (old)}, hout = new H.
+template <typename T, bool MUVAR>
+__global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T *hx_out, T *hy_out, T *hz_out)
+{
+    const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    band_node(b, p.n, t, i, j, k);
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    const int idx[3] = {i, j, k};
+    const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
+    T *outs[3] = {hx_out, hy_out, hz_out};
+    T hn[3];
+    bool have[3] = {i <= nx && j <= ny + 1 && k <= nz + 1, i <= nx + 1 && j <= ny && k <= nz + 1,
+                    i <= nx + 1 && j <= ny + 1 && k <= nz};
+    if (have[0]) hn[0] = h_node<T, 3, MUVAR>(p, idx, o, p.F[3][o]);
+    if (have[1]) hn[1] = h_node<T, 4, MUVAR>(p, idx, o, p.F[4][o]);
+    if (have[2]) hn[2] = h_node<T, 5, MUVAR>(p, idx, o, p.F[5][o]);
+    for (int c = 0; c < 3; ++c) {
+        if (!have[c]) continue;
+        outs[c][o] = hn[c];
+        for (int q = 0; q < p.nprb; ++q) {
+            const Prb &P = p.prb[q];
+            if (P.comp == 3 + c && P.i == i && P.j == j && P.k == k && p.probe_slot < p.probe_cap)
+                p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = hn[c];
+        }
+    }
+}
+
+// E^{n+1} on the band: p.F = {E^n (old), H^{n+1/2} (new)}, eout = new E.
+template <typename T, bool MUVAR>
+__global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T *ex_out, T *ey_out, T *ez_out)
+{
+    const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int i, j, k;
+    band_node(b, p.n, t, i, j, k);
+    const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
+    const int idx[3] = {i, j, k};
+    const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
+    unsigned sm = 0u;
+    for (int q = 0; q < p.nsrc; ++q)
+        if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) sm |= 1u << q;
+    const double t_half = ((double)p.step + 0.5) * p.dt;
+    T *outs[3] = {ex_out, ey_out, ez_out};
+    T en[3];
+    bool have[3] = {i <= nx + 1 && j <= ny && k <= nz, i <= nx && j <= ny + 1 && k <= nz,
+                    i <= nx && j <= ny && k <= nz + 1};
+    if (have[0]) en[0] = e_node<T, 0, MUVAR>(p, idx, o, p.F[0][o], sm, t_half);
+    if (have[1]) en[1] = e_node<T, 1, MUVAR>(p, idx, o, p.F[1][o], sm, t_half);
+    if (have[2]) en[2] = e_node<T, 2, MUVAR>(p, idx, o, p.F[2][o], sm, t_half);
+    for (int c = 0; c < 3; ++c) {
+        if (!have[c]) continue;
+        outs[c][o] = en[c];
+        for (int q = 0; q < p.nprb; ++q) {
+            const Prb &P = p.prb[q];
+            if (P.comp == c && P.i == i && P.j == j && P.k == k && p.probe_slot < p.probe_cap)
+                p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = en[c];
+        }
+    }
+}
+
+}  // namespace sbp

@@ -8,6 +8,12 @@
 // plane stay inside the allocation.  One linear offset o = k*sz + j*sy + i
 // addresses node (i, j, k) of every component; positions outside a
 // component's natural extents (Table I) stay zero.
+//
+// Two step paths.  FP32 blocks with uniform mu and at least 8 cells per axis
+// keep two field sets and advance with three launches per step (band_h,
+// fused_interior, band_e: old set -> new set, then swap).  Everything else
+// (FP64, varying mu, energy-monitor steps, the half-step calls) uses the
+// in-place h_update / e_update pair on the current set.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +26,7 @@
 
 #include "sbpsat.h"
 #include "kernels.cuh"
+#include "fused.cuh"
 
 namespace {
 
@@ -44,7 +51,16 @@ struct sbp_sim {
     size_t esize = 4;
     long long sy = 0, sz = 0;
     size_t field_elems = 0;               // elements per padded array, slack included
-    void *F[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *set[2][6] = {{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
+                       {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr}};
+    int cur = 0;                          // index of the set holding the current fields
+    bool fused_ok = false;                // second set allocated, fused path usable
+    bool fused_step = false;              // this step runs the fused path (set during a step)
+    int *error_flag = nullptr;            // device flag raised by a pipeline wait that gave up
+    sbp::FusedMaps maps[2];               // TMA tensor maps reading set 0 / set 1
+    int fused_kchunk = 32;
+    dim3 fused_grid;
+    sbp::Band band_hb, band_eb;
     float *eps = nullptr;
     float *mu = nullptr;
     double *partials = nullptr;
@@ -75,6 +91,9 @@ struct Layout {
     long long npartials;
     int kchunk;
     dim3 grid;
+    bool fused;
+    int fused_kchunk;
+    dim3 fused_grid;
     size_t total;
 };
 
@@ -123,7 +142,22 @@ Layout make_layout(const sbp_grid_desc *d)
     L.grid = dim3(gx, gy, gz);
     L.npartials = (long long)gx * gy * gz;
     L.partial_bytes = round_up((size_t)L.npartials * sizeof(double), 256);
-    L.total = 6 * L.field_bytes + L.cell_bytes * (d->mu_r ? 2 : 1) + L.partial_bytes + 256;
+    L.fused = d->precision == SBP_FP32 && !d->mu_r && d->nx >= 8 && d->ny >= 8 && d->nz >= 8 &&
+              !std::getenv("SBP_NO_FUSED");
+    if (L.fused) {
+        const int tx = (d->nx - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
+        const int ty = (d->ny - 5 + sbp::kFTY - 2) / (sbp::kFTY - 1);
+        const long long target = 4ll * 2 * 152;        // about four waves of two CTAs per SM
+        const long long chunks = std::max(1ll, (target + (long long)tx * ty - 1) / ((long long)tx * ty));
+        int kcf = (int)std::max(8ll, ((long long)(d->nz - 5) + chunks - 1) / chunks);
+        if (const char *env = std::getenv("SBP_FUSED_KCHUNK")) {
+            const int v = std::atoi(env);
+            if (v > 0) kcf = v;
+        }
+        L.fused_kchunk = kcf;
+        L.fused_grid = dim3(tx, ty, (d->nz - 5 + kcf - 1) / kcf);
+    }
+    L.total = (L.fused ? 12 : 6) * L.field_bytes + L.cell_bytes * (d->mu_r ? 2 : 1) + L.partial_bytes + 256 + 256;
     return L;
 }
 
@@ -138,6 +172,56 @@ int cuda_fail(cudaError_t e)
         cudaError_t e_ = (call);                \
         if (e_ != cudaSuccess) return cuda_fail(e_); \
     } while (0)
+
+// cuTensorMapEncodeTiled, fetched from the driver at run time (no link-time
+// dependency on libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+// 3D map over a padded FP32 array: dims (pitch, ny+2, nz+2), box (kFBX, rows, 1).
+int encode_one(CUtensorMap *m, void *base, const sbp_sim *s, int rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SBP_ECUDA;
+    const cuuint64_t dims[3] = {(cuuint64_t)s->sy, (cuuint64_t)(s->n[1] + 2), (cuuint64_t)(s->n[2] + 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)s->sy * 4, (cuuint64_t)s->sz * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)sbp::kFBX, (cuuint32_t)rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SBP_OK : SBP_ECUDA;
+}
+
+int encode_maps(sbp_sim *s)
+{
+    for (int set = 0; set < 2; set++) {
+        for (int f = 0; f < 3; f++) {
+            int rc = encode_one(&s->maps[set].e[f], s->set[set][f], s, sbp::kERows);
+            if (rc) return rc;
+            rc = encode_one(&s->maps[set].h[f], s->set[set][3 + f], s, sbp::kHRows);
+            if (rc) return rc;
+        }
+        int rc = encode_one(&s->maps[set].eps, s->eps, s, sbp::kHRows);
+        if (rc) return rc;
+    }
+    return SBP_OK;
+}
 
 int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
 {
@@ -154,12 +238,18 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     s->kchunk = L.kchunk;
     s->grid = L.grid;
     s->npartials = L.npartials;
+    s->fused_ok = L.fused;
+    s->fused_kchunk = L.fused_kchunk;
+    s->fused_grid = L.fused_grid;
     char *p = ws;
-    for (int c = 0; c < 6; c++) { s->F[c] = p; p += L.field_bytes; }
+    for (int set = 0; set < (L.fused ? 2 : 1); set++)
+        for (int c = 0; c < 6; c++) { s->set[set][c] = p; p += L.field_bytes; }
     s->eps = reinterpret_cast<float *>(p); p += L.cell_bytes;
     if (d->mu_r) { s->mu = reinterpret_cast<float *>(p); p += L.cell_bytes; }
     s->partials = reinterpret_cast<double *>(p); p += L.partial_bytes;
-    s->escalar = reinterpret_cast<double *>(p);
+    s->escalar = reinterpret_cast<double *>(p); p += 256;
+    s->error_flag = reinterpret_cast<int *>(p);
+    SBP_CUDA(cudaMemsetAsync(s->error_flag, 0, sizeof(int), s->stream));
 
     // coefficient build (a1): ghost-padded cell arrays on the device.  The
     // caller's cells are staged through the (still unused) Hx array.
@@ -172,7 +262,7 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
         if (m == 1 && !d->mu_r) break;
         float *stage = nullptr;
         if (host) {
-            stage = static_cast<float *>(s->F[3]);
+            stage = static_cast<float *>(s->set[0][3]);
             SBP_CUDA(cudaMemcpyAsync(stage, host, ncell * sizeof(float), cudaMemcpyHostToDevice, s->stream));
         }
         SBP_CUDA(cudaMemsetAsync(dst, 0, L.field_elems * sizeof(float), s->stream));
@@ -180,8 +270,22 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
         SBP_CUDA(cudaGetLastError());
         SBP_CUDA(cudaStreamSynchronize(s->stream));   // host cells may be released after return
     }
-    for (int c = 0; c < 6; c++) SBP_CUDA(cudaMemsetAsync(s->F[c], 0, L.field_elems * L.esize, s->stream));
+    for (int set = 0; set < (L.fused ? 2 : 1); set++)
+        for (int c = 0; c < 6; c++) SBP_CUDA(cudaMemsetAsync(s->set[set][c], 0, L.field_elems * L.esize, s->stream));
     SBP_CUDA(cudaStreamSynchronize(s->stream));
+    if (L.fused) {
+        int rc = encode_maps(s);
+        if (rc) return rc;
+        for (int phase = 0; phase < 2; phase++) {
+            sbp::Band &b = phase == 0 ? s->band_hb : s->band_eb;
+            b.lo = 3;
+            for (int a = 0; a < 3; a++) b.hi[a] = s->n[a] - (phase == 0 ? 2 : 3);
+            const long long ex = s->n[0] + 2, ey = s->n[1] + 2;
+            b.nz_slab = (long long)(b.lo + (s->n[2] + 1 - b.hi[2])) * ex * ey;
+            b.ny_slab = (long long)(b.hi[2] - b.lo + 1) * (b.lo + (s->n[1] + 1 - b.hi[1])) * ex;
+            b.nx_slab = (long long)(b.hi[2] - b.lo + 1) * (b.hi[1] - b.lo + 1) * (b.lo + (s->n[0] + 1 - b.hi[0]));
+        }
+    }
     return SBP_OK;
 }
 
@@ -194,11 +298,15 @@ sbp::Coef<T> split(double v)
     return c;
 }
 
+// Kernel parameters reading E from field set eset and H from set hset.
+// Interface partners: E from the partner's current set; H from the set the
+// partner's H^{n+1/2} lands in this step (its new set when it runs fused).
 template <typename T>
-int make_params(const sbp_sim *s, sbp::Params<T> &p)
+int make_params(const sbp_sim *s, sbp::Params<T> &p, int eset, int hset)
 {
     std::memset(&p, 0, sizeof(p));
-    for (int c = 0; c < 6; c++) p.F[c] = static_cast<T *>(s->F[c]);
+    for (int c = 0; c < 3; c++) p.F[c] = static_cast<T *>(s->set[eset][c]);
+    for (int c = 3; c < 6; c++) p.F[c] = static_cast<T *>(s->set[hset][c]);
     p.eps = s->eps;
     p.mu = s->mu;
     for (int a = 0; a < 3; a++) p.n[a] = s->n[a];
@@ -209,7 +317,9 @@ int make_params(const sbp_sim *s, sbp::Params<T> &p)
         if (s->face[f] == SBP_INTERFACE) {
             const sbp_sim *nb = s->nbr[f];
             if (!nb) return SBP_ESTATE;
-            for (int c = 0; c < 6; c++) p.link[f].F[c] = nb->F[c];
+            const int nh = nb->fused_step ? nb->cur ^ 1 : nb->cur;
+            for (int c = 0; c < 3; c++) p.link[f].F[c] = nb->set[nb->cur][c];
+            for (int c = 3; c < 6; c++) p.link[f].F[c] = nb->set[nh][c];
             p.link[f].sy = nb->sy;
             p.link[f].sz = nb->sz;
             p.link[f].n_norm = nb->n[f / 2];
@@ -244,7 +354,7 @@ template <typename T>
 int launch_h(const sbp_sim *s, bool energy, bool store)
 {
     sbp::Params<T> p;
-    int rc = make_params<T>(s, p);
+    int rc = make_params<T>(s, p, s->cur, s->cur);
     if (rc) return rc;
     const dim3 block(sbp::kBlockX, sbp::kBlockY);
     const bool muv = s->mu != nullptr;
@@ -266,7 +376,7 @@ template <typename T>
 int launch_e(const sbp_sim *s)
 {
     sbp::Params<T> p;
-    int rc = make_params<T>(s, p);
+    int rc = make_params<T>(s, p, s->cur, s->cur);
     if (rc) return rc;
     const dim3 block(sbp::kBlockX, sbp::kBlockY);
     if (s->mu) sbp::e_update<T, true><<<s->grid, block, 0, s->stream>>>(p);
@@ -282,6 +392,65 @@ int launch_h_any(const sbp_sim *s, bool energy, bool store)
 int launch_e_any(const sbp_sim *s)
 {
     return s->prec == SBP_FP64 ? launch_e<double>(s) : launch_e<float>(s);
+}
+
+// Fused path, phase 1: band H (old -> new) and the one-pass interior step.
+int launch_fused_phase1(sbp_sim *s)
+{
+    const int old = s->cur, nw = s->cur ^ 1;
+    sbp::Params<float> p;
+    int rc = make_params<float>(s, p, old, old);
+    if (rc) return rc;
+    const sbp::Band &bh = s->band_hb;
+    const long long tot = bh.nz_slab + bh.ny_slab + bh.nx_slab;
+    float **ns = reinterpret_cast<float **>(s->set[nw]);
+    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+    SBP_CUDA(cudaGetLastError());
+    sbp::FusedParams fp;
+    std::memset(&fp, 0, sizeof(fp));
+    for (int c = 0; c < 6; c++) fp.out[c] = ns[c];
+    for (int a = 0; a < 3; a++) { fp.n[a] = s->n[a]; fp.B[a] = p.B[a]; fp.A[a] = p.A[a]; }
+    fp.sy = s->sy;
+    fp.sz = s->sz;
+    fp.AJ = p.AJ;
+    fp.dt = p.dt;
+    fp.nsrc = p.nsrc;
+    for (int q = 0; q < p.nsrc; q++) fp.src[q] = p.src[q];
+    fp.nprb = p.nprb;
+    for (int q = 0; q < p.nprb; q++) fp.prb[q] = p.prb[q];
+    fp.probe_buf = p.probe_buf;
+    fp.probe_cap = p.probe_cap;
+    fp.probe_slot = p.probe_slot;
+    fp.step = p.step;
+    fp.kchunk = s->fused_kchunk;
+    fp.error_flag = s->error_flag;
+    static bool attr_set = false;
+    if (!attr_set) {
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
+        attr_set = true;
+    }
+    if (fp.nsrc > 0)
+        sbp::fused_interior<true><<<s->fused_grid, sbp::kFTY * 32, sbp::kFusedSmem, s->stream>>>(s->maps[old], fp);
+    else
+        sbp::fused_interior<false><<<s->fused_grid, sbp::kFTY * 32, sbp::kFusedSmem, s->stream>>>(s->maps[old], fp);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+// Fused path, phase 2: band E from E^n (old) and H^{n+1/2} (new) into the new set.
+int launch_fused_phase2(sbp_sim *s)
+{
+    const int old = s->cur, nw = s->cur ^ 1;
+    sbp::Params<float> p;
+    int rc = make_params<float>(s, p, old, nw);
+    if (rc) return rc;
+    const sbp::Band &be = s->band_eb;
+    const long long tot = be.nz_slab + be.ny_slab + be.nx_slab;
+    float **ns = reinterpret_cast<float **>(s->set[nw]);
+    sbp::band_e<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, be, ns[0], ns[1], ns[2]);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
 }
 
 int finalize_energy(const sbp_sim *s, double *dst)
@@ -392,12 +561,43 @@ int step_group(sbp_sim **sims, int nsims, int64_t nsteps)
         }
     }
     for (int64_t t = 0; t < nsteps; t++) {
-        rc = half_h(sims, nsims);
-        if (rc) return rc;
-        rc = half_e(sims, nsims);
-        if (rc) return rc;
+        // decide each block's path first: interface partners read it
+        for (int q = 0; q < nsims; q++) {
+            sbp_sim *s = sims[q];
+            const bool mon = s->energy_every > 0 && (s->step % s->energy_every) == 0;
+            s->fused_step = s->fused_ok && !mon;
+        }
+        for (int q = 0; q < nsims; q++) {
+            sbp_sim *s = sims[q];
+            rc = s->fused_step ? launch_fused_phase1(s) : half_h(&s, 1);
+            if (rc) return rc;
+        }
+        for (int q = 0; q < nsims; q++) {
+            sbp_sim *s = sims[q];
+            if (s->fused_step) {
+                rc = launch_fused_phase2(s);
+                if (rc) return rc;
+            } else {
+                rc = launch_e_any(s);
+                if (rc) return rc;
+            }
+        }
+        for (int q = 0; q < nsims; q++) {
+            sbp_sim *s = sims[q];
+            if (s->fused_step) s->cur ^= 1;
+            s->fused_step = false;
+            s->step++;
+        }
     }
     return SBP_OK;
+}
+
+int check_error_flag(sbp_sim *s)
+{
+    if (!s->error_flag) return SBP_OK;
+    int v = 0;
+    SBP_CUDA(cudaMemcpy(&v, s->error_flag, sizeof(int), cudaMemcpyDeviceToHost));
+    return v ? SBP_ETIMEOUT : SBP_OK;
 }
 
 }  // namespace
@@ -443,7 +643,7 @@ int sbp_set_field(sbp_sim *s, int comp, const void *src, int is_device)
     cudaSetDevice(s->device);
     cudaMemcpy3DParms m = {};
     m.srcPtr = make_cudaPitchedPtr(const_cast<void *>(src), e[0] * s->esize, e[0] * s->esize, e[1]);
-    m.dstPtr = make_cudaPitchedPtr(s->F[comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
+    m.dstPtr = make_cudaPitchedPtr(s->set[s->cur][comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
     m.extent = make_cudaExtent(e[0] * s->esize, e[1], e[2]);
     m.kind = cudaMemcpyDefault;
     SBP_CUDA(cudaMemcpy3DAsync(&m, s->stream));
@@ -457,12 +657,15 @@ int sbp_get_field(sbp_sim *s, int comp, void *dst, int to_device)
     if (!s || !dst || extents_of(s, comp, e)) return SBP_EINVAL;
     cudaSetDevice(s->device);
     cudaMemcpy3DParms m = {};
-    m.srcPtr = make_cudaPitchedPtr(s->F[comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
+    m.srcPtr = make_cudaPitchedPtr(s->set[s->cur][comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
     m.dstPtr = make_cudaPitchedPtr(dst, e[0] * s->esize, e[0] * s->esize, e[1]);
     m.extent = make_cudaExtent(e[0] * s->esize, e[1], e[2]);
     m.kind = cudaMemcpyDefault;
     SBP_CUDA(cudaMemcpy3DAsync(&m, s->stream));
-    if (!to_device) SBP_CUDA(cudaStreamSynchronize(s->stream));
+    if (!to_device) {
+        SBP_CUDA(cudaStreamSynchronize(s->stream));
+        return check_error_flag(s);
+    }
     return SBP_OK;
 }
 
@@ -608,7 +811,7 @@ int sbp_sync(sbp_sim *s)
     if (!s) return SBP_EINVAL;
     cudaSetDevice(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
-    return SBP_OK;
+    return check_error_flag(s);
 }
 
 double sbp_dt(const sbp_sim *s) { return s ? s->dt : 0.0; }

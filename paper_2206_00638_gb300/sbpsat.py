@@ -296,8 +296,11 @@ class Sim:
         return w.value
 
     def energy_series(self):
+        """(samples, rc): rc is 0 or SBP_EUNSTABLE (-4) when the monitor saw growth."""
         cnt = C.c_int64()
-        _check(lib().sbp_energy_series(self._h, None, 0, C.byref(cnt)), "sbp_energy_series")
+        rc = lib().sbp_energy_series(self._h, None, 0, C.byref(cnt))
+        if rc < 0 and rc != -4:
+            _check(rc, "sbp_energy_series")
         out = np.zeros(max(cnt.value, 1))
         rc = lib().sbp_energy_series(self._h, out.ctypes.data_as(C.POINTER(C.c_double)), cnt.value,
                                      C.byref(cnt))

@@ -181,3 +181,27 @@ def test_full_size_dielectric_256():
     errs, perr = _run_and_compare(w, w.steps, sbpsat.FP32)
     assert max(errs[0]) < 1e-5, errs
     assert perr < 1e-4
+
+
+@pytest.mark.parametrize("n", [(70, 43, 37), (130, 20, 17), (8, 8, 8), (9, 13, 10)])
+def test_fused_path_bitwise_equals_in_place_path(n, monkeypatch):
+    """The one-pass TMA step (interior) + band kernels give bit-identical fields and probes to
+    the in-place half-step kernels: same formulas, same rounding order."""
+    w = wl.random_box(n, faces=(A, P, M, A, P, M), seed=21, steps=37)
+    fused = parity.gpu_run(w, 37, sbpsat.FP32)[0]
+    monkeypatch.setenv("SBP_NO_FUSED", "1")
+    plain = parity.gpu_run(w, 37, sbpsat.FP32)[0]
+    for c in range(6):
+        assert np.array_equal(fused.field(c), plain.field(c)), c
+    assert np.array_equal(fused.probes(), plain.probes())
+    fused.close()
+    plain.close()
+
+
+def test_fused_path_with_energy_monitor_steps():
+    """Monitor steps run in place inside a fused run: parity with the oracle still holds."""
+    w = wl.random_box((48, 40, 33), faces=(P, A, M, P, A, M), seed=6, steps=90)
+    sims = parity.gpu_run(w, 90, sbpsat.FP32, energy_every=7)
+    blocks = parity.oracle_run(w, 90, sims[0].dt)
+    errs = parity.compare(sims, blocks)
+    assert max(errs[0]) < TOL[sbpsat.FP32], errs
