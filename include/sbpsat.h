@@ -157,6 +157,15 @@ int sbp_step_group(sbp_sim **sims, int nsims, int64_t nsteps);
 int sbp_half_step_h(sbp_sim **sims, int nsims);
 int sbp_half_step_e(sbp_sim **sims, int nsims);
 
+/* As sbp_step for one simulation, but brackets every kernel launch with CUDA
+ * events on the simulation's stream and, after synchronising, writes the
+ * average device time per launch (milliseconds) of each kernel kind to
+ * avg_ms[0..n_out-1] in the order: h_update, e_update, band_h,
+ * fused_interior, band_e (0 for kinds that did not run), and the number of
+ * launches per kind to launches[0..n_out-1] if non-NULL.  For measurement:
+ * the events add a small gap between launches. */
+int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out);
+
 /* Copy probe samples to host: out[p * cap + n] for probe p, sample n < cap.
  * Synchronises the stream.  *nsamples (optional) receives the number of
  * samples recorded per probe. */

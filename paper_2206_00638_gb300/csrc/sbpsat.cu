@@ -394,18 +394,14 @@ int launch_e_any(const sbp_sim *s)
     return s->prec == SBP_FP64 ? launch_e<double>(s) : launch_e<float>(s);
 }
 
-// Fused path, phase 1: band H (old -> new) and the one-pass interior step.
-int launch_fused_phase1(sbp_sim *s)
+// The one-pass interior step (old set -> new set).
+int launch_fused_interior_only(sbp_sim *s)
 {
     const int old = s->cur, nw = s->cur ^ 1;
     sbp::Params<float> p;
     int rc = make_params<float>(s, p, old, old);
     if (rc) return rc;
-    const sbp::Band &bh = s->band_hb;
-    const long long tot = bh.nz_slab + bh.ny_slab + bh.nx_slab;
     float **ns = reinterpret_cast<float **>(s->set[nw]);
-    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
-    SBP_CUDA(cudaGetLastError());
     sbp::FusedParams fp;
     std::memset(&fp, 0, sizeof(fp));
     for (int c = 0; c < 6; c++) fp.out[c] = ns[c];
@@ -436,6 +432,21 @@ int launch_fused_phase1(sbp_sim *s)
         sbp::fused_interior<false><<<s->fused_grid, sbp::kFTY * 32, sbp::kFusedSmem, s->stream>>>(s->maps[old], fp);
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
+}
+
+// Fused path, phase 1: band H (old -> new) and the one-pass interior step.
+int launch_fused_phase1(sbp_sim *s)
+{
+    const int old = s->cur, nw = s->cur ^ 1;
+    sbp::Params<float> p;
+    int rc = make_params<float>(s, p, old, old);
+    if (rc) return rc;
+    const sbp::Band &bh = s->band_hb;
+    const long long tot = bh.nz_slab + bh.ny_slab + bh.nx_slab;
+    float **ns = reinterpret_cast<float **>(s->set[nw]);
+    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+    SBP_CUDA(cudaGetLastError());
+    return launch_fused_interior_only(s);
 }
 
 // Fused path, phase 2: band E from E^n (old) and H^{n+1/2} (new) into the new set.
@@ -592,6 +603,74 @@ int step_group(sbp_sim **sims, int nsims, int64_t nsteps)
     return SBP_OK;
 }
 
+// sbp_step with CUDA events around every launch (kernel kinds: 0 h_update,
+// 1 e_update, 2 band_h, 3 fused_interior, 4 band_e).
+int step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out)
+{
+    constexpr int kKinds = 5;
+    double tot[kKinds] = {0, 0, 0, 0, 0};
+    long long cnt[kKinds] = {0, 0, 0, 0, 0};
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+    auto mark = [&](int k) -> int {
+        cudaEvent_t e;
+        SBP_CUDA(cudaEventCreate(&e));
+        SBP_CUDA(cudaEventRecord(e, s->stream));
+        ev.push_back(e);
+        kind.push_back(k);
+        return SBP_OK;
+    };
+    int rc = SBP_OK;
+    for (int64_t t = 0; t < nsteps && !rc; t++) {
+        const bool mon = s->energy_every > 0 && (s->step % s->energy_every) == 0;
+        s->fused_step = s->fused_ok && !mon && s->face[0] != SBP_INTERFACE && s->face[1] != SBP_INTERFACE &&
+                        s->face[2] != SBP_INTERFACE && s->face[3] != SBP_INTERFACE && s->face[4] != SBP_INTERFACE &&
+                        s->face[5] != SBP_INTERFACE;
+        if (s->fused_step) {
+            // phase 1 = band_h + fused_interior, launched separately to time each
+            const int old = s->cur, nw = s->cur ^ 1;
+            sbp::Params<float> p;
+            if ((rc = make_params<float>(s, p, old, old))) break;
+            const sbp::Band &bh = s->band_hb;
+            const long long tot_h = bh.nz_slab + bh.ny_slab + bh.nx_slab;
+            float **ns = reinterpret_cast<float **>(s->set[nw]);
+            if ((rc = mark(2))) break;
+            sbp::band_h<float, false><<<(unsigned)((tot_h + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+            if ((rc = mark(-1))) break;
+            // fused_interior alone: reuse phase 1 with the band launch skipped
+            if ((rc = mark(3))) break;
+            if ((rc = launch_fused_interior_only(s))) break;
+            if ((rc = mark(-1))) break;
+            if ((rc = mark(4))) break;
+            if ((rc = launch_fused_phase2(s))) break;
+            if ((rc = mark(-1))) break;
+            s->cur ^= 1;
+        } else {
+            if ((rc = mark(0))) break;
+            if ((rc = half_h(&s, 1))) break;
+            if ((rc = mark(-1))) break;
+            if ((rc = mark(1))) break;
+            if ((rc = launch_e_any(s))) break;
+            if ((rc = mark(-1))) break;
+        }
+        s->fused_step = false;
+        s->step++;
+    }
+    cudaStreamSynchronize(s->stream);
+    for (size_t q = 0; q + 1 < ev.size(); q += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+        tot[kind[q]] += ms;
+        cnt[kind[q]]++;
+    }
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    for (int k = 0; k < n_out && k < kKinds; k++) {
+        if (avg_ms) avg_ms[k] = cnt[k] ? tot[k] / cnt[k] : 0.0;
+        if (launches) launches[k] = cnt[k];
+    }
+    return rc;
+}
+
 int check_error_flag(sbp_sim *s)
 {
     if (!s->error_flag) return SBP_OK;
@@ -740,6 +819,19 @@ int sbp_half_step_e(sbp_sim **sims, int nsims)
 {
     int rc = check_group(sims, nsims);
     return rc ? rc : half_e(sims, nsims);
+}
+
+int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out)
+{
+    if (!s || nsteps < 0) return SBP_EINVAL;
+    sbp_sim *one[1] = {s};
+    int rc = check_group(one, 1);
+    if (rc) return rc;
+    if (s->energy_every > 0) {
+        rc = ensure_series(s, (s->step + nsteps) / s->energy_every + 1);
+        if (rc) return rc;
+    }
+    return step_timed(s, nsteps, avg_ms, launches, n_out);
 }
 
 int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples)

@@ -102,6 +102,7 @@ def lib():
                 "sbp_step_group": (I, [pp, I, I64]),
                 "sbp_half_step_h": (I, [pp, I]),
                 "sbp_half_step_e": (I, [pp, I]),
+                "sbp_step_timed": (I, [P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
                 "sbp_get_probes": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
                 "sbp_energy": (I, [P, C.POINTER(C.c_double)]),
                 "sbp_energy_group": (I, [pp, I, C.POINTER(C.c_double)]),
@@ -123,7 +124,7 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
-            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_series",
+            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_series",
             "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror"]
 
 
@@ -270,6 +271,15 @@ class Sim:
     # --- time stepping --------------------------------------------------
     def step(self, nsteps):
         _check(lib().sbp_step(self._h, int(nsteps)), "sbp_step")
+
+    KERNELS = ("h_update", "e_update", "band_h", "fused_interior", "band_e")
+
+    def step_timed(self, nsteps):
+        """Step with CUDA events around each launch: {kernel: (avg ms, launches)}."""
+        ms = (C.c_double * 5)()
+        cnt = (C.c_int64 * 5)()
+        _check(lib().sbp_step_timed(self._h, int(nsteps), ms, cnt, 5), "sbp_step_timed")
+        return {k: (ms[q], cnt[q]) for q, k in enumerate(self.KERNELS) if cnt[q]}
 
     def sync(self):
         _check(lib().sbp_sync(self._h), "sbp_sync")
