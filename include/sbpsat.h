@@ -178,6 +178,30 @@ int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples);
 int sbp_energy(sbp_sim *s, double *W);
 int sbp_energy_group(sbp_sim **sims, int nsims, double *W);
 
+/* Energy of one simulation for callers that must not allocate device memory.
+ * The paper has no counterpart: this is a library service.  Some callers
+ * cannot call cudaMalloc: a host function enqueued on a stream may not make
+ * CUDA calls that allocate, cudaFree synchronises the whole device, and some
+ * embedding frameworks fix the device budget up front.  This call computes
+ * the same W^n as sbp_energy with the same kernels, but keeps its per-CTA
+ * partial sums in a fixed array inside the library (SBP_NOALLOC_MAX_PARTIALS
+ * doubles = 512 KiB, held on every GPU that loads the library until the
+ * process exits) instead of the simulation's workspace, and writes W^n to
+ * the caller's device pointer W_dev (one double, 8-byte aligned) without
+ * synchronising.  Nothing is allocated and no allocating library routine is
+ * called.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Every call shares the array, and the array keeps the
+ * last call's partial sums: calls that overlap on the GPU (different streams
+ * without ordering) race and may return wrong values.  Each call rewrites
+ * every partial it reads, so nothing needs clearing between calls.  Errors:
+ * SBP_EINVAL (NULL arguments), SBP_ECAPACITY (with a message on stderr) if
+ * the grid needs more than SBP_NOALLOC_MAX_PARTIALS partial sums (one per
+ * CTA of the H-update grid; a cross-section of about 4000 x 4000 cells
+ * reaches the limit), SBP_ECUDA if the array's address cannot be obtained. */
+#define SBP_NOALLOC_MAX_PARTIALS 65536
+int sbp_energy_noalloc(sbp_sim *s, double *W_dev);
+
 /* Energy samples taken every desc.energy_every steps during sbp_step:
  * out[m] = W at step m * energy_every.  Synchronises.  Returns
  * SBP_EUNSTABLE if a sample is non-finite or exceeds 1.5x the first one

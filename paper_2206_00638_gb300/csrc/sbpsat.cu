@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -471,6 +472,53 @@ int finalize_energy(const sbp_sim *s, double *dst)
     return SBP_OK;
 }
 
+// Partial sums of sbp_energy_noalloc: a fixed array in this library, so that
+// call allocates nothing.  In host code the name is only a stand-in for the
+// symbol; its device address comes from cudaGetSymbolAddress, looked up once
+// per device with that device current.
+static __device__ __align__(256) double g_noalloc_partials[SBP_NOALLOC_MAX_PARTIALS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch(int device, double **out)
+{
+    if (device < 0 || device >= kMaxDevices) return SBP_EINVAL;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        if (e != cudaSuccess || !ptr) return SBP_ECUDA;
+        g_noalloc_addr[device] = static_cast<double *>(ptr);
+    }
+    *out = g_noalloc_addr[device];
+    return SBP_OK;
+}
+
+// The energy query of sbp_energy with the partial sums in `partials` and the
+// result written to the device pointer `dst`.
+template <typename T>
+int energy_into_t(const sbp_sim *s, double *partials, double *dst)
+{
+    sbp::Params<T> p;
+    int rc = make_params<T>(s, p, s->cur, s->cur);
+    if (rc) return rc;
+    p.partials = partials;
+    const dim3 block(sbp::kBlockX, sbp::kBlockY);
+    if (s->mu) sbp::h_update<T, true, false, true><<<s->grid, block, 0, s->stream>>>(p);
+    else sbp::h_update<T, true, false, false><<<s->grid, block, 0, s->stream>>>(p);
+    SBP_CUDA(cudaGetLastError());
+    sbp::energy_finalize<<<1, 256, 0, s->stream>>>(partials, s->npartials, dst);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+int energy_into(const sbp_sim *s, double *partials, double *dst)
+{
+    return s->prec == SBP_FP64 ? energy_into_t<double>(s, partials, dst) : energy_into_t<float>(s, partials, dst);
+}
+
 int ensure_series(sbp_sim *s, long long need)
 {
     if (need <= s->eseries_cap) return SBP_OK;
@@ -880,6 +928,21 @@ int sbp_energy(sbp_sim *s, double *W)
 {
     sbp_sim *one[1] = {s};
     return sbp_energy_group(one, 1, W);
+}
+
+int sbp_energy_noalloc(sbp_sim *s, double *W_dev)
+{
+    if (!s || !W_dev) return SBP_EINVAL;
+    if (s->npartials > SBP_NOALLOC_MAX_PARTIALS) {
+        std::fprintf(stderr, "sbp_energy_noalloc: grid needs %lld partial sums, limit %d\n",
+                     s->npartials, SBP_NOALLOC_MAX_PARTIALS);
+        return SBP_ECAPACITY;
+    }
+    cudaSetDevice(s->device);
+    double *scratch = nullptr;
+    int rc = noalloc_scratch(s->device, &scratch);
+    if (rc) return rc;
+    return energy_into(s, scratch, W_dev);
 }
 
 int sbp_energy_series(sbp_sim *s, double *out, int64_t cap, int64_t *count)

@@ -106,6 +106,7 @@ def lib():
                 "sbp_get_probes": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
                 "sbp_energy": (I, [P, C.POINTER(C.c_double)]),
                 "sbp_energy_group": (I, [pp, I, C.POINTER(C.c_double)]),
+                "sbp_energy_noalloc": (I, [P, P]),
                 "sbp_energy_series": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
                 "sbp_sync": (I, [P]),
                 "sbp_dt": (D, [P]),
@@ -124,7 +125,7 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
-            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_series",
+            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
             "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror"]
 
 
@@ -304,6 +305,14 @@ class Sim:
         w = C.c_double()
         _check(lib().sbp_energy(self._h, C.byref(w)), "sbp_energy")
         return w.value
+
+    def energy_noalloc(self, out):
+        """Write W^n into ``out`` (a CUDA float64 tensor with one element) on the simulation's
+        stream, without allocating device memory (scratch is a fixed array in the library)."""
+        if out.dtype.itemsize != 8 or not out.is_cuda:
+            raise ValueError("out must be a CUDA float64 tensor")
+        _check(lib().sbp_energy_noalloc(self._h, out.data_ptr()), "sbp_energy_noalloc")
+        return out
 
     def energy_series(self):
         """(samples, rc): rc is 0 or SBP_EUNSTABLE (-4) when the monitor saw growth."""
