@@ -298,40 +298,44 @@ struct Band {
     long long nz_slab, ny_slab, nx_slab;   // node counts of the three slabs
 };
 
-__device__ __forceinline__ void band_node(const Band &b, const int n[3], long long t, int &i, int &j, int &k)
+__device__ __forceinline__ void band_node(const Band &b, const int n[3], long long tl, int &i, int &j, int &k)
 {
-    const int ex = n[0] + 2, ey = n[1] + 2;
+    // 32-bit index arithmetic: every slab of a grid this library accepts has
+    // fewer than 2^32 nodes (the host checks), and 64-bit division is slow.
+    const unsigned ex = n[0] + 2, ey = n[1] + 2;
     const int lo = b.lo;
-    if (t < b.nz_slab) {
-        const long long plane = t / ((long long)ex * ey);
-        const long long r = t % ((long long)ex * ey);
-        k = plane < lo ? (int)plane : b.hi[2] + 1 + (int)(plane - lo);
+    unsigned t = (unsigned)tl;
+    if (tl < b.nz_slab) {
+        const unsigned plane = t / (ex * ey);
+        const unsigned r = t - plane * (ex * ey);
+        k = (int)plane < lo ? (int)plane : b.hi[2] + 1 + ((int)plane - lo);
         j = (int)(r / ex);
-        i = (int)(r % ex);
+        i = (int)(r - (unsigned)j * ex);
         return;
     }
-    t -= b.nz_slab;
-    const int ylo = lo, yhi_cnt = (n[1] + 1) - b.hi[1];   // rows above hi: hi+1 .. n+1
-    const int nyr = ylo + yhi_cnt;
-    if (t < b.ny_slab) {
-        const long long per_k = (long long)nyr * ex;
-        k = lo + (int)(t / per_k);
-        const long long r = t % per_k;
-        const int yr = (int)(r / ex);
-        j = yr < ylo ? yr : b.hi[1] + 1 + (yr - ylo);
-        i = (int)(r % ex);
+    t = (unsigned)(tl - b.nz_slab);
+    const unsigned nyr = lo + (n[1] + 1 - b.hi[1]);   // rows below lo and above hi
+    if (tl - b.nz_slab < b.ny_slab) {
+        const unsigned per_k = nyr * ex;
+        const unsigned kk = t / per_k;
+        const unsigned r = t - kk * per_k;
+        const unsigned yr = r / ex;
+        k = lo + (int)kk;
+        j = (int)yr < lo ? (int)yr : b.hi[1] + 1 + ((int)yr - lo);
+        i = (int)(r - yr * ex);
         return;
     }
-    t -= b.ny_slab;
-    const int xhi_cnt = (n[0] + 1) - b.hi[0];
-    const int nxr = lo + xhi_cnt;
-    const int nyin = b.hi[1] - lo + 1;
-    const long long per_k = (long long)nyin * nxr;
-    k = lo + (int)(t / per_k);
-    const long long r = t % per_k;
-    j = lo + (int)(r / nxr);
-    const int xr = (int)(r % nxr);
-    i = xr < lo ? xr : b.hi[0] + 1 + (xr - lo);
+    t = (unsigned)(tl - b.nz_slab - b.ny_slab);
+    const unsigned nxr = lo + (n[0] + 1 - b.hi[0]);
+    const unsigned nyin = b.hi[1] - lo + 1;
+    const unsigned per_k = nyin * nxr;
+    const unsigned kk = t / per_k;
+    const unsigned r = t - kk * per_k;
+    const unsigned yy = r / nxr;
+    const unsigned xr = r - yy * nxr;
+    k = lo + (int)kk;
+    j = lo + (int)yy;
+    i = (int)xr < lo ? (int)xr : b.hi[0] + 1 + ((int)xr - lo);
 }
 
 // H^{n+1/2} on the band: p.F = {E^n (old), H^{n-1/2} (old)}, hout = new H.

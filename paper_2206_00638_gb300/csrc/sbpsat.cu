@@ -61,6 +61,8 @@ struct sbp_sim {
     sbp::FusedMaps maps[2];               // TMA tensor maps reading set 0 / set 1
     int fused_kchunk = 32;
     dim3 fused_grid;
+    cudaStream_t side = nullptr;          // band_h runs here, concurrently with fused_interior
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     sbp::Band band_hb, band_eb;
     float *eps = nullptr;
     float *mu = nullptr;
@@ -277,6 +279,9 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     if (L.fused) {
         int rc = encode_maps(s);
         if (rc) return rc;
+        SBP_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+        SBP_CUDA(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
+        SBP_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
         for (int phase = 0; phase < 2; phase++) {
             sbp::Band &b = phase == 0 ? s->band_hb : s->band_eb;
             b.lo = 3;
@@ -285,6 +290,7 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
             b.nz_slab = (long long)(b.lo + (s->n[2] + 1 - b.hi[2])) * ex * ey;
             b.ny_slab = (long long)(b.hi[2] - b.lo + 1) * (b.lo + (s->n[1] + 1 - b.hi[1])) * ex;
             b.nx_slab = (long long)(b.hi[2] - b.lo + 1) * (b.hi[1] - b.lo + 1) * (b.lo + (s->n[0] + 1 - b.hi[0]));
+            if (b.nz_slab >= (1ll << 32) || b.ny_slab >= (1ll << 32) || b.nx_slab >= (1ll << 32)) return SBP_EINVAL;
         }
     }
     return SBP_OK;
@@ -435,7 +441,8 @@ int launch_fused_interior_only(sbp_sim *s)
     return SBP_OK;
 }
 
-// Fused path, phase 1: band H (old -> new) and the one-pass interior step.
+// Fused path, phase 1: band H (old -> new) on the side stream, concurrently
+// with the one-pass interior step on the main stream; joined before phase 2.
 int launch_fused_phase1(sbp_sim *s)
 {
     const int old = s->cur, nw = s->cur ^ 1;
@@ -445,9 +452,15 @@ int launch_fused_phase1(sbp_sim *s)
     const sbp::Band &bh = s->band_hb;
     const long long tot = bh.nz_slab + bh.ny_slab + bh.nx_slab;
     float **ns = reinterpret_cast<float **>(s->set[nw]);
-    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+    SBP_CUDA(cudaEventRecord(s->ev_fork, s->stream));
+    SBP_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->side>>>(p, bh, ns[3], ns[4], ns[5]);
     SBP_CUDA(cudaGetLastError());
-    return launch_fused_interior_only(s);
+    SBP_CUDA(cudaEventRecord(s->ev_join, s->side));
+    rc = launch_fused_interior_only(s);
+    if (rc) return rc;
+    SBP_CUDA(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+    return SBP_OK;
 }
 
 // Fused path, phase 2: band E from E^n (old) and H^{n+1/2} (new) into the new set.
@@ -981,6 +994,9 @@ int sbp_destroy(sbp_sim *s)
         sbp_sim *nb = s->nbr[f];
         if (nb && nb != s && s->nbr_face[f] >= 0 && nb->nbr[s->nbr_face[f]] == s) nb->nbr[s->nbr_face[f]] = nullptr;
     }
+    if (s->side) { cudaStreamSynchronize(s->side); cudaStreamDestroy(s->side); }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->probe_buf) cudaFree(s->probe_buf);
     if (s->eseries) cudaFree(s->eseries);
     if (s->own_ws && s->workspace) cudaFree(s->workspace);
