@@ -30,7 +30,10 @@ namespace sbp {
 constexpr int kFTX = 64;                 // H footprint width
 constexpr int kFTY = 8;                  // H footprint rows (= warps)
 constexpr int kFBX = kFTX + 4;           // TMA box width: x0-1 .. x0+63 from a 4-aligned start
-constexpr int kStages = 4;
+#ifndef SBP_FUSED_STAGES
+#define SBP_FUSED_STAGES 4
+#endif
+constexpr int kStages = SBP_FUSED_STAGES;     // TMA pipeline depth (planes in shared memory)
 constexpr int kERows = kFTY + 1;         // E rows y0-1 .. y0+7
 constexpr int kHRows = kFTY;             // H / eps rows y0 .. y0+7
 constexpr int kEField = 640;             // floats per E box slot (9*68 = 612, 128-byte rounded)
@@ -111,7 +114,7 @@ __device__ __forceinline__ void issue_plane(const FusedMaps &m, float *stage, ui
 }
 
 template <bool SRC>
-__global__ void __launch_bounds__(kFTY * 32, 2) fused_interior(const __grid_constant__ FusedMaps maps, const FusedParams p)
+__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interior(const __grid_constant__ FusedMaps maps, const FusedParams p)
 {
     extern __shared__ __align__(128) float smem[];
     float *hbuf = smem + kStages * kStageFloats;
@@ -159,38 +162,55 @@ __global__ void __launch_bounds__(kFTY * 32, 2) fused_interior(const __grid_cons
     bool ok = true;
     bool aborted = false;
     int waited = 0;                                   // load index of the next plane to wait for
+    // register carries of the previous plane (own columns): E^n, H^{n+1/2} and
+    // the eps cells (rows j, j+1; columns i, i+1) of that plane
+    float ec[2][3], hc[2][3], epc[2][4];
     if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0); waited = 1; }
-    for (int q = k0; q <= k1; ++q) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int re = (w + 1) * kFBX + cx0 + lane + 32 * h;
+#pragma unroll
+        for (int f = 0; f < 3; ++f) { ec[h][f] = smem[f * kEField + re]; hc[h][f] = 0.f; }
+#pragma unroll
+        for (int f = 0; f < 4; ++f) epc[h][f] = 0.f;
+    }
+    if (__syncthreads_or(!ok)) aborted = true;
+    if (!aborted && threadIdx.x == 0 && kStages < nplanes) {   // plane k0-1 is in registers now
+        issue_plane(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
+        ++issued;
+    }
+    for (int q = k0; q <= k1 && !aborted; ++q) {
         const int iq = q - k0 + 1;                   // load index of plane q
-        const int sq = iq % kStages, sm = (iq - 1) % kStages;
+        const int sq = iq % kStages;
         if (ok) ok = mbar_wait_bounded(&bar[sq], (iq / kStages) & 1);
         waited = iq + 1;
         const float *Sq = smem + sq * kStageFloats;   // plane q
-        const float *Sm = smem + sm * kStageFloats;   // plane q-1
         float *Hq = hbuf + (q & 1) * (3 * kFTY * kFTX);
         const float *Hp = hbuf + ((q - 1) & 1) * (3 * kFTY * kFTX);
+        const bool doE = q > k0 && rowE;
+        const int pl = q - 1;
 
-        // ---- H^{n+1/2} on plane q ------------------------------------------
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
             const int cc = cx0 + c;
+            const int i = x0 + c;
+            // ---- H^{n+1/2} at (i, j, q) --------------------------------------
             const int re = (w + 1) * kFBX + cc;           // E slot row of j
             const int rh = w * kFBX + cc;                 // H slot row of j
-            const float exq = Sq[0 * kEField + re], exm = Sm[0 * kEField + re], ex_jm = Sq[0 * kEField + re - kFBX];
-            const float eyq = Sq[1 * kEField + re], eym = Sm[1 * kEField + re], ey_im = Sq[1 * kEField + re - 1];
+            const float exq = Sq[0 * kEField + re], ex_jm = Sq[0 * kEField + re - kFBX];
+            const float eyq = Sq[1 * kEField + re], ey_im = Sq[1 * kEField + re - 1];
             const float ezq = Sq[2 * kEField + re], ez_im = Sq[2 * kEField + re - 1], ez_jm = Sq[2 * kEField + re - kFBX];
-            Acc<float> ax, ay, az;
-            ax.add(Bz, eyq - eym); ax.add(By, ezq - ez_jm, -1.f);
-            ay.add(Bx, ezq - ez_im); ay.add(Bz, exq - exm, -1.f);
-            az.add(By, exq - ex_jm); az.add(Bx, eyq - ey_im, -1.f);
-            const float hx = Sq[3 * kEField + 0 * kHField + rh] + plain_increment(ax);
-            const float hy = Sq[3 * kEField + 1 * kHField + rh] + plain_increment(ay);
-            const float hz = Sq[3 * kEField + 2 * kHField + rh] + plain_increment(az);
+            Acc<float> bx, by, bz;
+            bx.add(Bz, eyq - ec[h][1]); bx.add(By, ezq - ez_jm, -1.f);
+            by.add(Bx, ezq - ez_im);    by.add(Bz, exq - ec[h][0], -1.f);
+            bz.add(By, exq - ex_jm);    bz.add(Bx, eyq - ey_im, -1.f);
+            const float hx = Sq[3 * kEField + 0 * kHField + rh] + plain_increment(bx);
+            const float hy = Sq[3 * kEField + 1 * kHField + rh] + plain_increment(by);
+            const float hz = Sq[3 * kEField + 2 * kHField + rh] + plain_increment(bz);
             Hq[(0 * kFTY + w) * kFTX + c] = hx;
             Hq[(1 * kFTY + w) * kFTX + c] = hy;
             Hq[(2 * kFTY + w) * kFTX + c] = hz;
-            const int i = x0 + c;
             if (rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2) && (q < k1 || q == nz - 2)) {
                 const long long o = (long long)q * p.sz + (long long)j * p.sy + i;
                 p.out[3][o] = hx;
@@ -207,33 +227,28 @@ __global__ void __launch_bounds__(kFTY * 32, 2) fused_interior(const __grid_cons
                     }
                 }
             }
-        }
-        if (__syncthreads_or(!ok)) { aborted = true; break; }
+            // eps cells of plane q (rows j, j+1; columns i, i+1)
+            const float *eq = Sq + 3 * kEField + 3 * kHField;
+            const int r0 = w * kFBX + cc, r1 = r0 + kFBX;
+            const float q00 = eq[r0], q01 = eq[r1], q10 = eq[r0 + 1], q11 = eq[r1 + 1];
 
-        // ---- E^{n+1} on plane q-1 --------------------------------------------
-        if (q > k0 && rowE) {
-            const int pl = q - 1;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int c = lane + 32 * h;
-                const int i = x0 + c;
-                if (c >= kFTX - 1 || i > nx - 3) continue;
-                const int cc = cx0 + c;
-                const float hx = Hp[(0 * kFTY + w) * kFTX + c], hx_jp = Hp[(0 * kFTY + w + 1) * kFTX + c];
-                const float hy = Hp[(1 * kFTY + w) * kFTX + c], hy_ip = Hp[(1 * kFTY + w) * kFTX + c + 1];
-                const float hz = Hp[(2 * kFTY + w) * kFTX + c], hz_ip = Hp[(2 * kFTY + w) * kFTX + c + 1];
+            // ---- E^{n+1} at (i, j, q-1): neighbours' H of plane q-1 from shared
+            // memory (written last iteration), own H of planes q-1, q from registers
+            if (doE && c < kFTX - 1 && i <= nx - 3) {
+                const float hx_jp = Hp[(0 * kFTY + w + 1) * kFTX + c];
+                const float hy_ip = Hp[(1 * kFTY + w) * kFTX + c + 1];
+                const float hz_ip = Hp[(2 * kFTY + w) * kFTX + c + 1];
                 const float hz_jp = Hp[(2 * kFTY + w + 1) * kFTX + c];
-                const float hxn = Hq[(0 * kFTY + w) * kFTX + c], hyn = Hq[(1 * kFTY + w) * kFTX + c];
+                const float hxp = hc[h][0], hyp = hc[h][1], hzp = hc[h][2];
                 Acc<float> ax, ay, az;
-                ax.add(Ay, hz_jp - hz); ax.add(Az, hyn - hy, -1.f);
-                ay.add(Az, hxn - hx);   ay.add(Ax, hz_ip - hz, -1.f);
-                az.add(Ax, hy_ip - hy); az.add(Ay, hx_jp - hx, -1.f);
-                // eps cells: slot rows of j and j+1 on planes pl (Sm) and q (Sq)
-                const float *ep = Sm + 3 * kEField + 3 * kHField, *eq = Sq + 3 * kEField + 3 * kHField;
-                const int r0 = w * kFBX + cc, r1 = r0 + kFBX;
-                const float sx = (ep[r0] + ep[r1]) + (eq[r0] + eq[r1]);
-                const float sy = (ep[r0] + ep[r0 + 1]) + (eq[r0] + eq[r0 + 1]);
-                const float sz = (ep[r0] + ep[r0 + 1]) + (ep[r1] + ep[r1 + 1]);
+                ax.add(Ay, hz_jp - hzp); ax.add(Az, hy - hyp, -1.f);
+                ay.add(Az, hx - hxp);    ay.add(Ax, hz_ip - hzp, -1.f);
+                az.add(Ax, hy_ip - hyp); az.add(Ay, hx_jp - hxp, -1.f);
+                // node sums in the association of cell_sum
+                const float p00 = epc[h][0], p01 = epc[h][1], p10 = epc[h][2], p11 = epc[h][3];
+                const float sx = (p00 + p01) + (q00 + q01);
+                const float sy = (p00 + p10) + (q00 + q10);
+                const float sz = (p00 + p10) + (p01 + p11);
                 if (SRC && smask[h]) {
                     unsigned m = smask[h];
                     while (m) {
@@ -248,10 +263,9 @@ __global__ void __launch_bounds__(kFTY * 32, 2) fused_interior(const __grid_cons
                         }
                     }
                 }
-                const int re = (w + 1) * kFBX + cc;
-                const float ex = Sm[0 * kEField + re] + scaled_increment(ax, sx);
-                const float ey = Sm[1 * kEField + re] + scaled_increment(ay, sy);
-                const float ez = Sm[2 * kEField + re] + scaled_increment(az, sz);
+                const float ex = ec[h][0] + scaled_increment(ax, sx);
+                const float ey = ec[h][1] + scaled_increment(ay, sy);
+                const float ez = ec[h][2] + scaled_increment(az, sz);
                 const long long o = (long long)pl * p.sz + (long long)j * p.sy + i;
                 p.out[0][o] = ex;
                 p.out[1][o] = ey;
@@ -267,13 +281,17 @@ __global__ void __launch_bounds__(kFTY * 32, 2) fused_interior(const __grid_cons
                     }
                 }
             }
+            // carry plane q
+            ec[h][0] = exq; ec[h][1] = eyq; ec[h][2] = ezq;
+            hc[h][0] = hx; hc[h][1] = hy; hc[h][2] = hz;
+            epc[h][0] = q00; epc[h][1] = q01; epc[h][2] = q10; epc[h][3] = q11;
         }
-        __syncthreads();
-        // plane q-1 is consumed: refill its stage with plane q-1+kStages
+        // one barrier per plane: hbuf[q&1] complete, hbuf[(q-1)&1] and stage q free
+        if (__syncthreads_or(!ok)) { aborted = true; break; }
         if (threadIdx.x == 0) {
-            const int nxt = q - 1 + kStages;
+            const int nxt = q + kStages;
             if (nxt <= k1) {
-                issue_plane(maps, smem + sm * kStageFloats, &bar[sm], xb, y0, nxt);
+                issue_plane(maps, smem + sq * kStageFloats, &bar[sq], xb, y0, nxt);
                 ++issued;
             }
         }

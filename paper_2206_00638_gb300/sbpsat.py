@@ -58,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
         return LIB_PATH
     tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["nvcc", *NVCC_FLAGS, "-I" + _INC, "-I" + _CSRC, "-o", tmp, os.path.join(_CSRC, "sbpsat.cu")]
+    extra = os.environ.get("SBP_NVCC_FLAGS", "").split()   # tuning experiments only
+    cmd = ["nvcc", *NVCC_FLAGS, *extra, "-I" + _INC, "-I" + _CSRC, "-o", tmp, os.path.join(_CSRC, "sbpsat.cu")]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
