@@ -155,6 +155,17 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
     }
     const bool rowE = w < kFTY - 1 && j <= ny - 3;
     const bool rowH = j <= ny - 2 && (w < kFTY - 1 || j == ny - 2);
+    // per column: stores owned (H) / produced (E) by this thread, and the
+    // column's offset within a plane
+    bool colH[2], colE[2];
+    long long obase[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h, i = x0 + c;
+        colH[h] = rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2);
+        colE[h] = rowE && c < kFTX - 1 && i <= nx - 3;
+        obase[h] = (long long)j * p.sy + i;
+    }
     const Coef<float> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
     const Coef<float> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
     const double t_half = ((double)p.step + 0.5) * p.dt;
@@ -164,7 +175,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
     int waited = 0;                                   // load index of the next plane to wait for
     // register carries of the previous plane (own columns): E^n, H^{n+1/2} and
     // the eps cells (rows j, j+1; columns i, i+1) of that plane
-    float ec[2][3], hc[2][3], epc[2][4];
+    float ec[2][3], hc[2][3], epc[2][3];
     if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0); waited = 1; }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -172,7 +183,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
 #pragma unroll
         for (int f = 0; f < 3; ++f) { ec[h][f] = smem[f * kEField + re]; hc[h][f] = 0.f; }
 #pragma unroll
-        for (int f = 0; f < 4; ++f) epc[h][f] = 0.f;
+        for (int f = 0; f < 3; ++f) epc[h][f] = 0.f;
     }
     if (__syncthreads_or(!ok)) aborted = true;
     if (!aborted && threadIdx.x == 0 && kStages < nplanes) {   // plane k0-1 is in registers now
@@ -187,7 +198,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
         const float *Sq = smem + sq * kStageFloats;   // plane q
         float *Hq = hbuf + (q & 1) * (3 * kFTY * kFTX);
         const float *Hp = hbuf + ((q - 1) & 1) * (3 * kFTY * kFTX);
-        const bool doE = q > k0 && rowE;
+        const bool doE = q > k0;
         const int pl = q - 1;
 
 #pragma unroll
@@ -211,8 +222,8 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
             Hq[(0 * kFTY + w) * kFTX + c] = hx;
             Hq[(1 * kFTY + w) * kFTX + c] = hy;
             Hq[(2 * kFTY + w) * kFTX + c] = hz;
-            if (rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2) && (q < k1 || q == nz - 2)) {
-                const long long o = (long long)q * p.sz + (long long)j * p.sy + i;
+            if (colH[h] && (q < k1 || q == nz - 2)) {
+                const long long o = (long long)q * p.sz + obase[h];
                 p.out[3][o] = hx;
                 p.out[4][o] = hy;
                 p.out[5][o] = hz;
@@ -227,14 +238,16 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
                     }
                 }
             }
-            // eps cells of plane q (rows j, j+1; columns i, i+1)
+            // eps cells of plane q (rows j, j+1; columns i, i+1), as the pair sums
+            // the node sums of cell_sum are built from: (a+b)+(c+d)
             const float *eq = Sq + 3 * kEField + 3 * kHField;
             const int r0 = w * kFBX + cc, r1 = r0 + kFBX;
             const float q00 = eq[r0], q01 = eq[r1], q10 = eq[r0 + 1], q11 = eq[r1 + 1];
+            const float qa = q00 + q01, qb = q00 + q10, qc = q01 + q11;
 
             // ---- E^{n+1} at (i, j, q-1): neighbours' H of plane q-1 from shared
             // memory (written last iteration), own H of planes q-1, q from registers
-            if (doE && c < kFTX - 1 && i <= nx - 3) {
+            if (doE && colE[h]) {
                 const float hx_jp = Hp[(0 * kFTY + w + 1) * kFTX + c];
                 const float hy_ip = Hp[(1 * kFTY + w) * kFTX + c + 1];
                 const float hz_ip = Hp[(2 * kFTY + w) * kFTX + c + 1];
@@ -244,11 +257,11 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
                 ax.add(Ay, hz_jp - hzp); ax.add(Az, hy - hyp, -1.f);
                 ay.add(Az, hx - hxp);    ay.add(Ax, hz_ip - hzp, -1.f);
                 az.add(Ax, hy_ip - hyp); az.add(Ay, hx_jp - hxp, -1.f);
-                // node sums in the association of cell_sum
-                const float p00 = epc[h][0], p01 = epc[h][1], p10 = epc[h][2], p11 = epc[h][3];
-                const float sx = (p00 + p01) + (q00 + q01);
-                const float sy = (p00 + p10) + (q00 + q10);
-                const float sz = (p00 + p10) + (p01 + p11);
+                // node sums in the association of cell_sum:
+                //   Ex (m + m_y) + (m_z + m_yz), Ey (m + m_x) + (m_z + m_xz), Ez (m + m_x) + (m_y + m_xy)
+                const float sx = epc[h][0] + qa;
+                const float sy = epc[h][1] + qb;
+                const float sz = epc[h][1] + epc[h][2];
                 if (SRC && smask[h]) {
                     unsigned m = smask[h];
                     while (m) {
@@ -266,7 +279,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
                 const float ex = ec[h][0] + scaled_increment(ax, sx);
                 const float ey = ec[h][1] + scaled_increment(ay, sy);
                 const float ez = ec[h][2] + scaled_increment(az, sz);
-                const long long o = (long long)pl * p.sz + (long long)j * p.sy + i;
+                const long long o = (long long)pl * p.sz + obase[h];
                 p.out[0][o] = ex;
                 p.out[1][o] = ey;
                 p.out[2][o] = ez;
@@ -284,7 +297,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
             // carry plane q
             ec[h][0] = exq; ec[h][1] = eyq; ec[h][2] = ezq;
             hc[h][0] = hx; hc[h][1] = hy; hc[h][2] = hz;
-            epc[h][0] = q00; epc[h][1] = q01; epc[h][2] = q10; epc[h][3] = q11;
+            epc[h][0] = qa; epc[h][1] = qb; epc[h][2] = qc;
         }
         // one barrier per plane: hbuf[q&1] complete, hbuf[(q-1)&1] and stage q free
         if (__syncthreads_or(!ok)) { aborted = true; break; }

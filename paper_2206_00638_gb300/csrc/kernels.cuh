@@ -145,15 +145,26 @@ __device__ __forceinline__ T dminus_row(const T *__restrict__ u, long long s, in
     if (r == n + 1) return u[n * s] - u[(n - 1) * s];
     return u[r * s] - u[(r - 1) * s];          // rows 1, 3..n-2, n
 }
-// D+ : x- (n+2 values) -> x+ (n+1 rows).
-template <typename T>
-__device__ __forceinline__ T dplus_row(const T *__restrict__ v, long long s, int r, int n)
+// Field load; CG = true reads through L2 only (ld.global.cg), for values this
+// kernel itself wrote earlier (coherent across the threads of a CTA after a
+// barrier, never served stale from L1 or the read-only path).
+template <bool CG, typename T>
+__device__ __forceinline__ T ldf(const T *p)
 {
-    if (r == 0) return T(0.5) * (v[s] + v[2 * s]) - v[0];
-    if (r == 1) return T(0.75) * v[2 * s] - T(0.5) * v[0] - T(0.25) * v[s];
-    if (r == n - 1) return T(0.25) * v[n * s] + T(0.5) * v[(n + 1) * s] - T(0.75) * v[(n - 1) * s];
-    if (r == n) return v[(n + 1) * s] - T(0.5) * (v[(n - 1) * s] + v[n * s]);
-    return v[(r + 1) * s] - v[r * s];          // rows 2..n-2
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// D+ : x- (n+2 values) -> x+ (n+1 rows).
+template <typename T, bool CG = false>
+__device__ __forceinline__ T dplus_row(const T *v, long long s, int r, int n)
+{
+    if (r == 0) return T(0.5) * (ldf<CG>(v + s) + ldf<CG>(v + 2 * s)) - ldf<CG>(v);
+    if (r == 1) return T(0.75) * ldf<CG>(v + 2 * s) - T(0.5) * ldf<CG>(v) - T(0.25) * ldf<CG>(v + s);
+    if (r == n - 1)
+        return T(0.25) * ldf<CG>(v + n * s) + T(0.5) * ldf<CG>(v + (n + 1) * s) - T(0.75) * ldf<CG>(v + (n - 1) * s);
+    if (r == n) return ldf<CG>(v + (n + 1) * s) - T(0.5) * (ldf<CG>(v + (n - 1) * s) + ldf<CG>(v + n * s));
+    return ldf<CG>(v + (r + 1) * s) - ldf<CG>(v + r * s);          // rows 2..n-2
 }
 
 // 1D norm weight (unit spacing) of node r: P+ = diag(1/2,1,...,1,1/2),
@@ -316,7 +327,7 @@ __device__ __forceinline__ T h_node(const Params<T> &p, const int idx[3], long l
 }
 
 // E half-step: general path for one component at one node.
-template <typename T, int C, bool MUVAR>
+template <typename T, int C, bool MUVAR, bool CG = false>
 __device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long long o, T eold,
                                     unsigned smask, double t_half)
 {
@@ -328,7 +339,7 @@ __device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long l
         const int u = curl_comp(C, t), a = curl_axis(C, t), sg = curl_sign(t);
         const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
         const T *line = p.F[u] + (o - idx[a] * st);
-        const T d = dplus_row(line, st, idx[a], p.n[a]);
+        const T d = dplus_row<T, CG>(line, st, idx[a], p.n[a]);
         acc.add(p.A[a], d, T(sg));
         // E on the plus grid along a: face nodes at 0 and n carry the SAT
         if (idx[a] == 0 || idx[a] == p.n[a]) {
@@ -337,7 +348,7 @@ __device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long l
             const int type = p.face[f];
             if (type != kPEC) {
                 const T phi = T(-sg * side);
-                const T pv = line[(side < 0 ? 0 : p.n[a] + 1) * st];
+                const T pv = ldf<CG>(line + (side < 0 ? 0 : p.n[a] + 1) * st);
                 if (type == kPMC) {
                     acc.add(p.A[a], pv, T(2) * phi);
                 } else if (type == kABS) {
@@ -354,7 +365,7 @@ __device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long l
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
                     for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
-                    acc.add(p.A[a], pv - nf[on], phi);
+                    acc.add(p.A[a], pv - ldf<CG>(nf + on), phi);
                 }
             }
         }
