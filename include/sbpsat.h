@@ -166,6 +166,31 @@ int sbp_half_step_e(sbp_sim **sims, int nsims);
  * the events add a small gap between launches. */
 int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out);
 
+/* Batches: continuous batching of many simulations.  A batch advances all
+ * its member simulations together, one kernel launch per kernel kind per
+ * step covering every member (a tile table over the members), so many small
+ * grids fill the GPU as one large launch.  Each member keeps its own fields,
+ * sources, probes and step count and gives bit-identical results to
+ * stepping it alone with sbp_step.  Members must be single-block FP32
+ * simulations with uniform mu, at least 8 cells per axis, no interface
+ * faces and no energy monitor, created on the batch's stream.  The step
+ * index lives in device memory, so with use_graphs != 0 a chunk of steps is
+ * captured once as a CUDA graph and replayed while the membership and chunk
+ * length stay the same. */
+typedef struct sbp_batch sbp_batch;
+int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out);
+/* Add s, to stop after nsteps more steps.  The batch does not own s; remove
+ * it (or destroy the batch) before destroying s. */
+int sbp_batch_add(sbp_batch *b, sbp_sim *s, int64_t nsteps);
+int sbp_batch_remove(sbp_batch *b, sbp_sim *s);
+/* Steps s still has to take in this batch. */
+int sbp_batch_remaining(const sbp_batch *b, const sbp_sim *s, int64_t *remaining);
+/* Advance every member by min(nsteps, its remaining steps), asynchronously
+ * on the batch's stream. */
+int sbp_batch_step(sbp_batch *b, int64_t nsteps);
+int sbp_batch_size(const sbp_batch *b);
+int sbp_batch_destroy(sbp_batch *b);
+
 /* Copy probe samples to host: out[p * cap + n] for probe p, sample n < cap.
  * Synchronises the stream.  *nsamples (optional) receives the number of
  * samples recorded per probe. */

@@ -113,18 +113,20 @@ __device__ __forceinline__ void issue_plane(const FusedMaps &m, float *stage, ui
     tma_load_3d(stage + 3 * kEField + 3 * kHField, &m.eps, xb, y0, plane, bar);
 }
 
+// One CTA of the one-pass interior step: tile (bx, by) in x/y, z-chunk bz,
+// time step `step` (J is evaluated at t^{step+1/2}), probe sample `pslot`.
 template <bool SRC>
-__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interior(const __grid_constant__ FusedMaps maps, const FusedParams p)
+__device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedParams &p, long long step, long long pslot,
+                                           int bx, int by, int bz, float *smem)
 {
-    extern __shared__ __align__(128) float smem[];
     float *hbuf = smem + kStages * kStageFloats;
     uint64_t *bar = reinterpret_cast<uint64_t *>(hbuf + kHbufFloats);
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
-    const int x0 = 3 + blockIdx.x * (kFTX - 1);
-    const int y0 = 3 + blockIdx.y * (kFTY - 1);
-    const int k0 = 3 + blockIdx.z * p.kchunk;
+    const int x0 = 3 + bx * (kFTX - 1);
+    const int y0 = 3 + by * (kFTY - 1);
+    const int k0 = 3 + bz * p.kchunk;
     const int k1 = min(k0 + p.kchunk, nz - 2);       // E planes [k0, k1); H planes [k0, k1]
     const int xb = (x0 - 1) & ~3;
     const int cx0 = x0 - xb;                          // smem column of x0, in 1..4
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
     }
     const Coef<float> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
     const Coef<float> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
-    const double t_half = ((double)p.step + 0.5) * p.dt;
+    const double t_half = ((double)step + 0.5) * p.dt;
 
     bool ok = true;
     bool aborted = false;
@@ -233,8 +235,8 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
                         const int b = __ffsll(m) - 1;
                         m &= m - 1;
                         const Prb &P = p.prb[b];
-                        if (P.k == q && P.comp >= 3 && p.probe_slot < p.probe_cap)
-                            p.probe_buf[(long long)b * p.probe_cap + p.probe_slot] = P.comp == 3 ? hx : P.comp == 4 ? hy : hz;
+                        if (P.k == q && P.comp >= 3 && pslot < p.probe_cap)
+                            p.probe_buf[(long long)b * p.probe_cap + pslot] = P.comp == 3 ? hx : P.comp == 4 ? hy : hz;
                     }
                 }
             }
@@ -289,8 +291,8 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
                         const int b = __ffsll(m) - 1;
                         m &= m - 1;
                         const Prb &P = p.prb[b];
-                        if (P.k == pl && P.comp < 3 && p.probe_slot < p.probe_cap)
-                            p.probe_buf[(long long)b * p.probe_cap + p.probe_slot] = P.comp == 0 ? ex : P.comp == 1 ? ey : ez;
+                        if (P.k == pl && P.comp < 3 && pslot < p.probe_cap)
+                            p.probe_buf[(long long)b * p.probe_cap + pslot] = P.comp == 0 ? ex : P.comp == 1 ? ey : ez;
                     }
                 }
             }
@@ -316,6 +318,13 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
         for (int L = waited > 0 ? waited - 1 : 0; L < issued; ++L)
             (void)mbar_wait_bounded(&bar[L % kStages], (L / kStages) & 1);
     }
+}
+
+template <bool SRC>
+__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interior(const __grid_constant__ FusedMaps maps, const FusedParams p)
+{
+    extern __shared__ __align__(128) float smem[];
+    fused_body<SRC>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -369,19 +378,16 @@ __device__ __forceinline__ void band_node(const Band &b, const int n[3], long lo
     i = (int)xr < lo ? (int)xr : b.hi[0] + 1 + ((int)xr - lo);
 }
 
-// H^{n+1/2} on the band: p.F = {E^n (old), H^{n-1/2} (old)}, hout = new H.
+// H^{n+1/2} at band node t: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
 template <typename T, bool MUVAR>
-__global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T *hx_out, T *hy_out, T *hz_out)
+__device__ __forceinline__ void band_h_node(const Params<T> &p, const Band &b, long long t, long long pslot,
+                                            T *const outs[3])
 {
-    const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= total) return;
     int i, j, k;
     band_node(b, p.n, t, i, j, k);
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int idx[3] = {i, j, k};
     const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
-    T *outs[3] = {hx_out, hy_out, hz_out};
     T hn[3];
     bool have[3] = {i <= nx && j <= ny + 1 && k <= nz + 1, i <= nx + 1 && j <= ny && k <= nz + 1,
                     i <= nx + 1 && j <= ny + 1 && k <= nz};
@@ -393,19 +399,27 @@ __global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T
         outs[c][o] = hn[c];
         for (int q = 0; q < p.nprb; ++q) {
             const Prb &P = p.prb[q];
-            if (P.comp == 3 + c && P.i == i && P.j == j && P.k == k && p.probe_slot < p.probe_cap)
-                p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = hn[c];
+            if (P.comp == 3 + c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
+                p.probe_buf[(long long)q * p.probe_cap + pslot] = hn[c];
         }
     }
 }
 
-// E^{n+1} on the band: p.F = {E^n (old), H^{n+1/2} (new)}, eout = new E.
 template <typename T, bool MUVAR>
-__global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T *ex_out, T *ey_out, T *ez_out)
+__global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T *hx_out, T *hy_out, T *hz_out)
 {
     const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= total) return;
+    T *const outs[3] = {hx_out, hy_out, hz_out};
+    band_h_node<T, MUVAR>(p, b, t, p.probe_slot, outs);
+}
+
+// E^{n+1} at band node t: p.F = {E^n (old), H^{n+1/2} (new)}, outs = new E.
+template <typename T, bool MUVAR>
+__device__ __forceinline__ void band_e_node(const Params<T> &p, const Band &b, long long t, long long step,
+                                            long long pslot, T *const outs[3])
+{
     int i, j, k;
     band_node(b, p.n, t, i, j, k);
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -414,8 +428,7 @@ __global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T
     unsigned sm = 0u;
     for (int q = 0; q < p.nsrc; ++q)
         if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) sm |= 1u << q;
-    const double t_half = ((double)p.step + 0.5) * p.dt;
-    T *outs[3] = {ex_out, ey_out, ez_out};
+    const double t_half = ((double)step + 0.5) * p.dt;
     T en[3];
     bool have[3] = {i <= nx + 1 && j <= ny && k <= nz, i <= nx && j <= ny + 1 && k <= nz,
                     i <= nx && j <= ny && k <= nz + 1};
@@ -427,10 +440,110 @@ __global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T
         outs[c][o] = en[c];
         for (int q = 0; q < p.nprb; ++q) {
             const Prb &P = p.prb[q];
-            if (P.comp == c && P.i == i && P.j == j && P.k == k && p.probe_slot < p.probe_cap)
-                p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = en[c];
+            if (P.comp == c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
+                p.probe_buf[(long long)q * p.probe_cap + pslot] = en[c];
         }
     }
+}
+
+template <typename T, bool MUVAR>
+__global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T *ex_out, T *ey_out, T *ez_out)
+{
+    const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    T *const outs[3] = {ex_out, ey_out, ez_out};
+    band_e_node<T, MUVAR>(p, b, t, p.step, p.probe_slot, outs);
+}
+
+// ---------------------------------------------------------------------------
+// Batched step: one launch per kernel kind advances every grid of a batch
+// (continuous batching of many simulations).  A CTA finds its grid in a
+// prefix table of CTA counts; the grid's parameters and TMA maps live in
+// global memory; the step index comes from a device counter, so a captured
+// chunk of K steps can be replayed (the launches of a chunk carry offsets
+// 0..K-1 and batch_advance adds the steps taken).  Grids that reached their
+// target step skip their work, so a chunk may end a grid early.
+// ---------------------------------------------------------------------------
+struct BatchGrid {
+    FusedMaps maps[2];            // TMA maps reading field set 0 / set 1
+    FusedParams fp[2];            // fp[c]: reads set c, writes set c^1
+    Params<float> ph[2];          // band H, current set c
+    Params<float> pe[2];          // band E: E of set c, H of set c^1
+    float *hout[2][3], *eout[2][3];   // new-set outputs when the current set is c
+    Band bh, be;
+    long long *counter;           // steps taken (device)
+    long long target;             // the grid stops when the counter reaches this
+    long long cstart;             // counter value at which the current set was cur0
+    long long probe_base;
+    int cur0;
+    int tiles[3];
+};
+
+__device__ __forceinline__ int find_slot(const int *pre, int n, int b)
+{
+    int lo = 0, hi = n - 1;                 // largest g with pre[g] <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool batch_state(const BatchGrid &g, int offset, long long &step, int &par)
+{
+    step = *g.counter + offset;
+    if (step >= g.target) return false;
+    par = (g.cur0 + (int)((step - g.cstart) & 1)) & 1;
+    return true;
+}
+
+__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_batched(const BatchGrid *G, const int *pre, int n,
+                                                                                  int offset)
+{
+    extern __shared__ __align__(128) float smem[];
+    const int g = find_slot(pre, n, blockIdx.x);
+    const BatchGrid &B = G[g];
+    long long step;
+    int par;
+    if (!batch_state(B, offset, step, par)) return;
+    const int local = blockIdx.x - pre[g];
+    const int tx = B.tiles[0], ty = B.tiles[1];
+    fused_body<true>(B.maps[par], B.fp[par], step, step - B.probe_base, local % tx, (local / tx) % ty, local / (tx * ty),
+                     smem);
+}
+
+__global__ void __launch_bounds__(256) band_h_batched(const BatchGrid *G, const int *pre, int n, int offset)
+{
+    const int g = find_slot(pre, n, blockIdx.x);
+    const BatchGrid &B = G[g];
+    long long step;
+    int par;
+    if (!batch_state(B, offset, step, par)) return;
+    const long long t = (long long)(blockIdx.x - pre[g]) * blockDim.x + threadIdx.x;
+    if (t >= B.bh.nz_slab + B.bh.ny_slab + B.bh.nx_slab) return;
+    band_h_node<float, false>(B.ph[par], B.bh, t, step - B.probe_base, B.hout[par]);
+}
+
+__global__ void __launch_bounds__(256) band_e_batched(const BatchGrid *G, const int *pre, int n, int offset)
+{
+    const int g = find_slot(pre, n, blockIdx.x);
+    const BatchGrid &B = G[g];
+    long long step;
+    int par;
+    if (!batch_state(B, offset, step, par)) return;
+    const long long t = (long long)(blockIdx.x - pre[g]) * blockDim.x + threadIdx.x;
+    if (t >= B.be.nz_slab + B.be.ny_slab + B.be.nx_slab) return;
+    band_e_node<float, false>(B.pe[par], B.be, t, step, step - B.probe_base, B.eout[par]);
+}
+
+__global__ void batch_advance(const BatchGrid *G, int n, long long k)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const long long c = *G[g].counter, t = G[g].target;
+    *G[g].counter = c + k < t ? c + k : (c < t ? t : c);
 }
 
 }  // namespace sbp

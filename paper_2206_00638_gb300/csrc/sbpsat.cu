@@ -16,6 +16,9 @@
 // in-place h_update / e_update pair on the current set.
 #include <cuda_runtime.h>
 
+#include <climits>
+#include <cstdint>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -402,14 +405,13 @@ int launch_e_any(const sbp_sim *s)
 }
 
 // The one-pass interior step (old set -> new set).
-int launch_fused_interior_only(sbp_sim *s)
+// Parameters of the one-pass interior step reading set `old`, writing set old^1.
+int make_fused_params(const sbp_sim *s, int old, sbp::FusedParams &fp)
 {
-    const int old = s->cur, nw = s->cur ^ 1;
     sbp::Params<float> p;
     int rc = make_params<float>(s, p, old, old);
     if (rc) return rc;
-    float **ns = reinterpret_cast<float **>(s->set[nw]);
-    sbp::FusedParams fp;
+    float **ns = reinterpret_cast<float **>(const_cast<void **>(s->set[old ^ 1]));
     std::memset(&fp, 0, sizeof(fp));
     for (int c = 0; c < 6; c++) fp.out[c] = ns[c];
     for (int a = 0; a < 3; a++) { fp.n[a] = s->n[a]; fp.B[a] = p.B[a]; fp.A[a] = p.A[a]; }
@@ -427,12 +429,32 @@ int launch_fused_interior_only(sbp_sim *s)
     fp.step = p.step;
     fp.kchunk = s->fused_kchunk;
     fp.error_flag = s->error_flag;
-    static bool attr_set = false;
-    if (!attr_set) {
+    return SBP_OK;
+}
+
+int set_fused_smem_attr()
+{
+    static bool done[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !done[dev]) {
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
-        attr_set = true;
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
+        done[dev] = true;
     }
+    return SBP_OK;
+}
+
+// The one-pass interior step (old set -> new set).
+int launch_fused_interior_only(sbp_sim *s)
+{
+    const int old = s->cur;
+    sbp::FusedParams fp;
+    int rc = make_fused_params(s, old, fp);
+    if (rc) return rc;
+    rc = set_fused_smem_attr();
+    if (rc) return rc;
     if (fp.nsrc > 0)
         sbp::fused_interior<true><<<s->fused_grid, sbp::kFTY * 32, sbp::kFusedSmem, s->stream>>>(s->maps[old], fp);
     else
@@ -742,6 +764,118 @@ int check_error_flag(sbp_sim *s)
 
 }  // namespace
 
+// A batch: many single-block FP32 simulations advanced together, one launch
+// per kernel kind per step for all of them (see BatchGrid in fused.cuh).
+struct sbp_batch {
+    struct Member {
+        sbp_sim *s;
+        long long target;        // absolute step index at which the member stops
+    };
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::vector<Member> m;
+    sbp::BatchGrid *d_grids = nullptr;
+    int *d_pre = nullptr;               // three prefix tables of cap+1 ints: fused, band H, band E
+    long long *d_counters = nullptr;
+    int cap = 0;
+    int nf = 0, nh = 0, ne = 0;         // CTAs per launch
+    bool dirty = true;
+    bool use_graph = true;
+    cudaGraphExec_t gexec = nullptr;
+    long long gK = 0;
+};
+
+namespace {
+
+int batch_reserve(sbp_batch *b, int n)
+{
+    if (n <= b->cap) return SBP_OK;
+    const int cap = std::max(n, 2 * b->cap + 4);
+    SBP_CUDA(cudaStreamSynchronize(b->stream));
+    if (b->d_grids) cudaFree(b->d_grids);
+    if (b->d_pre) cudaFree(b->d_pre);
+    if (b->d_counters) cudaFree(b->d_counters);
+    b->d_grids = nullptr; b->d_pre = nullptr; b->d_counters = nullptr;
+    SBP_CUDA(cudaMalloc(&b->d_grids, sizeof(sbp::BatchGrid) * cap));
+    SBP_CUDA(cudaMalloc(&b->d_pre, sizeof(int) * 3 * (cap + 1)));
+    SBP_CUDA(cudaMalloc(&b->d_counters, sizeof(long long) * cap));
+    b->cap = cap;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    return SBP_OK;
+}
+
+// Upload every member's parameters, prefix tables and step counters.
+int batch_rebuild(sbp_batch *b)
+{
+    const int n = (int)b->m.size();
+    int rc = batch_reserve(b, std::max(n, 1));
+    if (rc) return rc;
+    std::vector<sbp::BatchGrid> hg(std::max(n, 1));
+    std::vector<int> pre(3 * (b->cap + 1), 0);
+    std::vector<long long> cnt(std::max(n, 1), 0);
+    int *pf = pre.data(), *ph = pre.data() + (b->cap + 1), *pe = pre.data() + 2 * (b->cap + 1);
+    for (int g = 0; g < n; g++) {
+        sbp_sim *s = b->m[g].s;
+        sbp::BatchGrid &G = hg[g];
+        std::memset(&G, 0, sizeof(G));
+        for (int c = 0; c < 2; c++) {
+            G.maps[c] = s->maps[c];
+            if ((rc = make_fused_params(s, c, G.fp[c]))) return rc;
+            if ((rc = make_params<float>(s, G.ph[c], c, c))) return rc;
+            if ((rc = make_params<float>(s, G.pe[c], c, c ^ 1))) return rc;
+            for (int f = 0; f < 3; f++) {
+                G.hout[c][f] = static_cast<float *>(s->set[c ^ 1][3 + f]);
+                G.eout[c][f] = static_cast<float *>(s->set[c ^ 1][f]);
+            }
+        }
+        G.bh = s->band_hb;
+        G.be = s->band_eb;
+        G.counter = b->d_counters + g;
+        G.target = b->m[g].target;
+        G.cstart = s->step;
+        G.probe_base = s->probe_base;
+        G.cur0 = s->cur;
+        G.tiles[0] = s->fused_grid.x; G.tiles[1] = s->fused_grid.y; G.tiles[2] = s->fused_grid.z;
+        cnt[g] = s->step;
+        const long long nfg = (long long)s->fused_grid.x * s->fused_grid.y * s->fused_grid.z;
+        const long long nhg = (G.bh.nz_slab + G.bh.ny_slab + G.bh.nx_slab + 255) / 256;
+        const long long neg = (G.be.nz_slab + G.be.ny_slab + G.be.nx_slab + 255) / 256;
+        if ((long long)pf[g] + nfg > INT32_MAX || (long long)ph[g] + nhg > INT32_MAX || (long long)pe[g] + neg > INT32_MAX)
+            return SBP_ECAPACITY;
+        pf[g + 1] = pf[g] + (int)nfg;
+        ph[g + 1] = ph[g] + (int)nhg;
+        pe[g + 1] = pe[g] + (int)neg;
+    }
+    b->nf = pf[n]; b->nh = ph[n]; b->ne = pe[n];
+    if (n > 0) {
+        SBP_CUDA(cudaMemcpyAsync(b->d_grids, hg.data(), sizeof(sbp::BatchGrid) * n, cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaMemcpyAsync(b->d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaMemcpyAsync(b->d_counters, cnt.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaStreamSynchronize(b->stream));   // host staging buffers are released on return
+    }
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    b->dirty = false;
+    return SBP_OK;
+}
+
+// K steps of every member: offsets 0..K-1, then the counters advance by K.
+int batch_launch_chunk(sbp_batch *b, long long K)
+{
+    const int n = (int)b->m.size();
+    const int *pf = b->d_pre, *ph = b->d_pre + (b->cap + 1), *pe = b->d_pre + 2 * (b->cap + 1);
+    for (long long o = 0; o < K; o++) {
+        if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->stream>>>(b->d_grids, ph, n, (int)o);
+        if (b->nf > 0)
+            sbp::fused_batched<<<b->nf, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(b->d_grids, pf, n, (int)o);
+        if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->stream>>>(b->d_grids, pe, n, (int)o);
+    }
+    sbp::batch_advance<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_grids, n, K);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 size_t sbp_workspace_bytes(const sbp_grid_desc *desc)
@@ -1001,6 +1135,105 @@ int sbp_destroy(sbp_sim *s)
     if (s->eseries) cudaFree(s->eseries);
     if (s->own_ws && s->workspace) cudaFree(s->workspace);
     delete s;
+    return SBP_OK;
+}
+
+int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
+{
+    if (!out) return SBP_EINVAL;
+    sbp_batch *b = new (std::nothrow) sbp_batch();
+    if (!b) return SBP_ENOMEM;
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+    b->use_graph = use_graphs != 0;
+    cudaGetDevice(&b->device);
+    int rc = set_fused_smem_attr();
+    if (rc) { delete b; return rc; }
+    *out = b;
+    return SBP_OK;
+}
+
+int sbp_batch_add(sbp_batch *b, sbp_sim *s, int64_t nsteps)
+{
+    if (!b || !s || nsteps < 0) return SBP_EINVAL;
+    if (!s->fused_ok || s->stream != b->stream || s->energy_every > 0 || s->device != b->device) return SBP_EINVAL;
+    for (int f = 0; f < 6; f++)
+        if (s->face[f] == SBP_INTERFACE) return SBP_EINVAL;
+    for (auto &m : b->m)
+        if (m.s == s) return SBP_ESTATE;
+    b->m.push_back({s, s->step + nsteps});
+    b->dirty = true;
+    return SBP_OK;
+}
+
+int sbp_batch_remove(sbp_batch *b, sbp_sim *s)
+{
+    if (!b || !s) return SBP_EINVAL;
+    for (size_t g = 0; g < b->m.size(); g++)
+        if (b->m[g].s == s) {
+            b->m.erase(b->m.begin() + g);
+            b->dirty = true;
+            return SBP_OK;
+        }
+    return SBP_EINVAL;
+}
+
+int sbp_batch_remaining(const sbp_batch *b, const sbp_sim *s, int64_t *remaining)
+{
+    if (!b || !s || !remaining) return SBP_EINVAL;
+    for (auto &m : b->m)
+        if (m.s == s) {
+            *remaining = m.target - s->step;
+            return SBP_OK;
+        }
+    return SBP_EINVAL;
+}
+
+int sbp_batch_step(sbp_batch *b, int64_t nsteps)
+{
+    if (!b || nsteps < 0) return SBP_EINVAL;
+    cudaSetDevice(b->device);
+    if (b->m.empty() || nsteps == 0) return SBP_OK;
+    int rc = SBP_OK;
+    if (b->dirty && (rc = batch_rebuild(b))) return rc;
+    if (b->use_graph) {
+        if (!b->gexec || b->gK != nsteps) {
+            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            SBP_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            rc = batch_launch_chunk(b, nsteps);
+            cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
+            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+            if (e != cudaSuccess) return SBP_ECUDA;
+            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { b->gexec = nullptr; return SBP_ECUDA; }
+            b->gK = nsteps;
+        }
+        SBP_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+    } else {
+        if ((rc = batch_launch_chunk(b, nsteps))) return rc;
+    }
+    // host bookkeeping: every member took min(nsteps, remaining) steps
+    for (auto &m : b->m) {
+        const long long done = std::min<long long>(nsteps, std::max<long long>(0, m.target - m.s->step));
+        m.s->step += done;
+        m.s->cur ^= (int)(done & 1);
+    }
+    return SBP_OK;
+}
+
+int sbp_batch_size(const sbp_batch *b) { return b ? (int)b->m.size() : 0; }
+
+int sbp_batch_destroy(sbp_batch *b)
+{
+    if (!b) return SBP_EINVAL;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->d_grids) cudaFree(b->d_grids);
+    if (b->d_pre) cudaFree(b->d_pre);
+    if (b->d_counters) cudaFree(b->d_counters);
+    delete b;
     return SBP_OK;
 }
 

@@ -114,6 +114,13 @@ def lib():
                 "sbp_step_index": (I64, [P]),
                 "sbp_destroy": (I, [P]),
                 "sbp_strerror": (C.c_char_p, [I]),
+                "sbp_batch_create": (I, [P, I, pp]),
+                "sbp_batch_add": (I, [P, P, I64]),
+                "sbp_batch_remove": (I, [P, P]),
+                "sbp_batch_remaining": (I, [P, P, C.POINTER(C.c_int64)]),
+                "sbp_batch_step": (I, [P, I64]),
+                "sbp_batch_size": (I, [P]),
+                "sbp_batch_destroy": (I, [P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -127,7 +134,9 @@ def exported_symbols() -> Sequence[str]:
     return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
             "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
-            "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror"]
+            "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
+            "sbp_batch_create", "sbp_batch_add", "sbp_batch_remove", "sbp_batch_remaining", "sbp_batch_step",
+            "sbp_batch_size", "sbp_batch_destroy"]
 
 
 def _strerror(code: int) -> str:
@@ -366,3 +375,42 @@ def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_ever
     for a, fa, b, fb in w.links:
         sims[a].connect(fa, sims[b], fb)
     return sims
+
+
+class Batch:
+    """Continuous batching of many simulations: one launch per kernel kind per step covers every
+    member (wraps ``sbp_batch``).  Members must be created on the batch's stream."""
+
+    def __init__(self, stream=None, use_graphs=True):
+        self.stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        _check(lib().sbp_batch_create(self.stream, 1 if use_graphs else 0, C.byref(h)), "sbp_batch_create")
+        self._h = h.value
+        self.members = []
+
+    def add(self, sim: Sim, nsteps: int):
+        _check(lib().sbp_batch_add(self._h, sim.handle, int(nsteps)), "sbp_batch_add")
+        self.members.append(sim)
+
+    def remove(self, sim: Sim):
+        _check(lib().sbp_batch_remove(self._h, sim.handle), "sbp_batch_remove")
+        self.members.remove(sim)
+
+    def remaining(self, sim: Sim) -> int:
+        r = C.c_int64()
+        _check(lib().sbp_batch_remaining(self._h, sim.handle, C.byref(r)), "sbp_batch_remaining")
+        return r.value
+
+    def step(self, nsteps: int):
+        _check(lib().sbp_batch_step(self._h, int(nsteps)), "sbp_batch_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sbp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
