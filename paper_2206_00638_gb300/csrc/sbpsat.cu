@@ -173,10 +173,15 @@ int cuda_fail(cudaError_t e)
     return SBP_ECUDA;
 }
 
+// On failure, also consume the runtime's last-error slot so that a
+// non-sticky error is not reported again by a later, unrelated call.
 #define SBP_CUDA(call)                          \
     do {                                        \
         cudaError_t e_ = (call);                \
-        if (e_ != cudaSuccess) return cuda_fail(e_); \
+        if (e_ != cudaSuccess) {                \
+            (void)cudaGetLastError();           \
+            return cuda_fail(e_);               \
+        }                                       \
     } while (0)
 
 // cuTensorMapEncodeTiled, fetched from the driver at run time (no link-time
@@ -772,6 +777,7 @@ struct sbp_batch {
         long long target;        // absolute step index at which the member stops
     };
     cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;         // private stream the graph is captured on (capture runs nothing)
     int device = 0;
     std::vector<Member> m;
     sbp::BatchGrid *d_grids = nullptr;
@@ -1148,6 +1154,11 @@ int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
     cudaGetDevice(&b->device);
     int rc = set_fused_smem_attr();
     if (rc) { delete b; return rc; }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete b;
+        return SBP_ECUDA;
+    }
     *out = b;
     return SBP_OK;
 }
@@ -1198,15 +1209,24 @@ int sbp_batch_step(sbp_batch *b, int64_t nsteps)
     if (b->use_graph) {
         if (!b->gexec || b->gK != nsteps) {
             if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+            // record the chunk on the private stream (nothing executes during
+            // capture), then launch the graph on the batch's stream, which may
+            // be the legacy default stream that cannot itself be captured
             cudaGraph_t graph = nullptr;
-            SBP_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            SBP_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            cudaStream_t keep = b->stream;
+            b->stream = b->cap;
             rc = batch_launch_chunk(b, nsteps);
-            cudaError_t e = cudaStreamEndCapture(b->stream, &graph);
-            if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
-            if (e != cudaSuccess) return SBP_ECUDA;
+            b->stream = keep;
+            cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+            if (rc || e != cudaSuccess) {
+                (void)cudaGetLastError();
+                if (graph) cudaGraphDestroy(graph);
+                return rc ? rc : SBP_ECUDA;
+            }
             e = cudaGraphInstantiate(&b->gexec, graph, 0);
             cudaGraphDestroy(graph);
-            if (e != cudaSuccess) { b->gexec = nullptr; return SBP_ECUDA; }
+            if (e != cudaSuccess) { (void)cudaGetLastError(); b->gexec = nullptr; return SBP_ECUDA; }
             b->gK = nsteps;
         }
         SBP_CUDA(cudaGraphLaunch(b->gexec, b->stream));
@@ -1230,6 +1250,7 @@ int sbp_batch_destroy(sbp_batch *b)
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap) cudaStreamDestroy(b->cap);
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_pre) cudaFree(b->d_pre);
     if (b->d_counters) cudaFree(b->d_counters);
