@@ -207,7 +207,6 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         for (int h = 0; h < 2; ++h) {
             const int c = lane + 32 * h;
             const int cc = cx0 + c;
-            const int i = x0 + c;
             // ---- H^{n+1/2} at (i, j, q) --------------------------------------
             const int re = (w + 1) * kFBX + cc;           // E slot row of j
             const int rh = w * kFBX + cc;                 // H slot row of j

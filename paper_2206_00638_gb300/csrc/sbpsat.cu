@@ -777,7 +777,7 @@ struct sbp_batch {
         long long target;        // absolute step index at which the member stops
     };
     cudaStream_t stream = nullptr;
-    cudaStream_t cap = nullptr;         // private stream the graph is captured on (capture runs nothing)
+    cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on (capture runs nothing)
     int device = 0;
     std::vector<Member> m;
     sbp::BatchGrid *d_grids = nullptr;
@@ -1154,7 +1154,7 @@ int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
     cudaGetDevice(&b->device);
     int rc = set_fused_smem_attr();
     if (rc) { delete b; return rc; }
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         (void)cudaGetLastError();
         delete b;
         return SBP_ECUDA;
@@ -1213,12 +1213,12 @@ int sbp_batch_step(sbp_batch *b, int64_t nsteps)
             // capture), then launch the graph on the batch's stream, which may
             // be the legacy default stream that cannot itself be captured
             cudaGraph_t graph = nullptr;
-            SBP_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+            SBP_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
             cudaStream_t keep = b->stream;
-            b->stream = b->cap;
+            b->stream = b->cap_stream;
             rc = batch_launch_chunk(b, nsteps);
             b->stream = keep;
-            cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+            cudaError_t e = cudaStreamEndCapture(b->cap_stream, &graph);
             if (rc || e != cudaSuccess) {
                 (void)cudaGetLastError();
                 if (graph) cudaGraphDestroy(graph);
@@ -1250,7 +1250,7 @@ int sbp_batch_destroy(sbp_batch *b)
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_pre) cudaFree(b->d_pre);
     if (b->d_counters) cudaFree(b->d_counters);
