@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=["dielectric", "serve"], default="dielectric")
+    ap.add_argument("--requests", type=int, default=512, help="serving workload: number of requests")
+    ap.add_argument("--rho", type=float, default=0.9, help="serving workload: offered load / plain throughput")
+    ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--budget-gib", type=float, default=8.0)
     return ap.parse_args()
 
 
@@ -319,10 +324,91 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_serve(args):
+    """Serving workload: the request stream processed (1) one grid per launch sequence, in order
+    (the plain FP32 path), (2) by the continuous-batching server with every request submitted at
+    once, (3) by the server with Poisson arrivals at rho times the plain throughput.  End to end
+    per request: creation and material upload, all steps, probe samples back to the host."""
+    import random
+
+    import numpy as np
+    import torch
+
+    from paper_2206_00638_gb300 import sbpsat
+    from paper_2206_00638_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    reqs = wl.serving_requests(nreq=args.requests, seed=4)
+    work = [int(np.prod(r["n"])) * r["steps"] for r in reqs]
+    total = float(sum(work))
+    stream = torch.cuda.Stream()
+
+    # (1) plain: one grid at a time through sbp_step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in reqs:
+        spec = wl.serving_spec(r)
+        s = sbpsat.Sim(spec.n, spec.h, spec.faces, eps_r=spec.eps_r, cfl=0.95, stream=stream)
+        for src in spec.sources:
+            s.add_source(src.comp, src.i, src.j, src.k, src.kind, src.amp, src.tw, src.t0, src.f)
+        for p in spec.probes:
+            s.add_probe(p.comp, p.i, p.j, p.k)
+        s.reserve_probes(r["steps"])
+        s.step(r["steps"])
+        s.probes()
+        s.close()
+    plain_s = time.perf_counter() - t0
+    plain = total / plain_s / 1e9
+
+    def serve(arrivals):
+        srv = sbpsat.Server(stream=stream, budget_bytes=int(args.budget_gib * 2 ** 30), max_slots=args.slots,
+                            chunk=32)
+        specs = [wl.serving_spec(r) for r in reqs[:0]]  # materialised lazily below
+        tickets = []
+        start = time.perf_counter()
+        for q, r in enumerate(reqs):
+            if arrivals is not None:
+                delay = start + arrivals[q] - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+            tickets.append(srv.submit(wl.serving_spec(r), r["steps"]))
+        srv.drain()
+        res = [srv.poll(t) for t in tickets]
+        cu, span = srv.stats()
+        lat = np.array([x.done_s - x.submit_s for x in res]) * 1e3
+        bad = sum(1 for x in res if x.status != 0)
+        srv.close()
+        return cu / span / 1e9, float(np.percentile(lat, 50)), float(np.percentile(lat, 99)), bad
+
+    closed_v, closed_p50, closed_p99, bad1 = serve(None)
+    rate = args.rho * plain * 1e9 / (total / len(reqs))      # requests per second
+    rnd = random.Random(4)
+    t, arr = 0.0, []
+    for _ in reqs:
+        t += rnd.expovariate(rate)
+        arr.append(t)
+    open_v, p50, p99, bad2 = serve(arr)
+    line = {
+        "metric": "Gcell-updates/s (serving, aggregate, end to end)", "value": closed_v, "unit": "Gcell-updates/s",
+        "n_gpus": 1, "steps": len(reqs), "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"serving_stream_{len(reqs)}req", "cells_per_axis": "U{32..192}",
+                   "steps": "U{500..4000}", "slots": args.slots, "hbm_budget_gib": args.budget_gib, "chunk_steps": 32},
+        "plain_one_grid_per_launch": plain, "batched_over_plain": closed_v / plain,
+        "poisson": {"rho": args.rho, "requests_per_s": rate, "aggregate": open_v, "p50_ms": p50, "p99_ms": p99},
+        "closed_p50_ms": closed_p50, "closed_p99_ms": closed_p99, "failed_requests": bad1 + bad2,
+        "total_cell_updates": total,
+    }
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

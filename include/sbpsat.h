@@ -45,6 +45,7 @@ extern "C" {
 #define SBP_ENOTCONFORMING (-6)  /* interface faces do not share their node sets     */
 #define SBP_ESTATE (-7)          /* call not valid in the current state              */
 #define SBP_ECAPACITY (-8)       /* buffer too small (probes, workspace)             */
+#define SBP_EAGAIN (-9)          /* result not ready yet (server poll)               */
 
 typedef enum { SBP_PEC = 0, SBP_PMC = 1, SBP_ABSORBING = 2, SBP_INTERFACE = 3 } sbp_face_t;
 typedef enum { SBP_FP32 = 0, SBP_FP64 = 1, SBP_FP32_FP16STORE = 2 } sbp_precision_t;
@@ -190,6 +191,51 @@ int sbp_batch_remaining(const sbp_batch *b, const sbp_sim *s, int64_t *remaining
 int sbp_batch_step(sbp_batch *b, int64_t nsteps);
 int sbp_batch_size(const sbp_batch *b);
 int sbp_batch_destroy(sbp_batch *b);
+
+/* Serving: a request loop with continuous batching.  Requests are
+ * admitted in arrival order as slots (max_slots) and device memory (the
+ * HBM budget, capped by the free memory at creation) free up; admitted
+ * requests join the running batch at the next chunk boundary, so their work
+ * overlaps on the device with the requests already running; finished
+ * requests leave the batch, their probe samples are copied out and their
+ * memory is returned to the stream-ordered pool.  A scheduler thread owned
+ * by the server does all device work on the server's stream; results are
+ * identical to running each request alone.  Times are seconds on the
+ * server's monotonic clock. */
+typedef struct sbp_source_desc { int32_t comp, i, j, k, waveform; double amp, tw, t0, f; } sbp_source_desc;
+typedef struct sbp_probe_desc { int32_t comp, i, j, k; } sbp_probe_desc;
+typedef struct sbp_request {
+    sbp_grid_desc grid;              /* FP32, eligible for batching (see sbp_batch_add); the
+                                        eps_r / mu_r arrays are copied at submit */
+    int64_t nsteps;
+    int32_t nsources;
+    const sbp_source_desc *sources;  /* copied at submit */
+    int32_t nprobes;
+    const sbp_probe_desc *probes;    /* copied at submit */
+} sbp_request;
+typedef struct sbp_result {
+    int32_t status;                  /* SBP_OK or the error that ended the request */
+    int64_t steps;                   /* steps taken */
+    double submit_s, admit_s, done_s;
+    int32_t nprobes;
+} sbp_result;
+typedef struct sbp_server sbp_server;
+/* hbm_budget_bytes = 0: use 90 % of the free device memory.  chunk_steps:
+ * steps per batched launch sequence (a captured graph). */
+int sbp_server_create(void *cuda_stream, size_t hbm_budget_bytes, int max_slots, int chunk_steps, sbp_server **out);
+int sbp_server_submit(sbp_server *srv, const sbp_request *req, uint64_t *ticket);
+/* SBP_OK and *res filled when the request is done, SBP_EAGAIN otherwise. */
+int sbp_server_poll(sbp_server *srv, uint64_t ticket, sbp_result *res);
+/* Probe samples of a finished request: out[p * cap + n]. */
+int sbp_server_probes(sbp_server *srv, uint64_t ticket, double *out, int64_t cap);
+/* Forget a finished request (its probe samples are released). */
+int sbp_server_release(sbp_server *srv, uint64_t ticket);
+/* Block until every submitted request is done. */
+int sbp_server_drain(sbp_server *srv);
+/* Cell-updates done so far and the time span from the first submit to the
+ * last completion. */
+int sbp_server_stats(sbp_server *srv, double *cell_updates, double *span_s);
+int sbp_server_destroy(sbp_server *srv);
 
 /* Copy probe samples to host: out[p * cap + n] for probe p, sample n < cap.
  * Synchronises the stream.  *nsamples (optional) receives the number of

@@ -64,6 +64,7 @@ struct sbp_sim {
     sbp::FusedMaps maps[2];               // TMA tensor maps reading set 0 / set 1
     int fused_kchunk = 32;
     dim3 fused_grid;
+    bool async_setup = false;             // caller keeps host inputs alive: no stream syncs in setup
     cudaStream_t side = nullptr;          // band_h runs here, concurrently with fused_interior
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     sbp::Band band_hb, band_eb;
@@ -279,11 +280,11 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
         SBP_CUDA(cudaMemsetAsync(dst, 0, L.field_elems * sizeof(float), s->stream));
         sbp::pad_cells<<<blocks, threads, 0, s->stream>>>(stage, d->nx, d->ny, d->nz, 1.0f, dst, L.sy, L.sz);
         SBP_CUDA(cudaGetLastError());
-        SBP_CUDA(cudaStreamSynchronize(s->stream));   // host cells may be released after return
+        if (!s->async_setup) SBP_CUDA(cudaStreamSynchronize(s->stream));   // host cells may be released after return
     }
     for (int set = 0; set < (L.fused ? 2 : 1); set++)
         for (int c = 0; c < 6; c++) SBP_CUDA(cudaMemsetAsync(s->set[set][c], 0, L.field_elems * L.esize, s->stream));
-    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    if (!s->async_setup) SBP_CUDA(cudaStreamSynchronize(s->stream));
     if (L.fused) {
         int rc = encode_maps(s);
         if (rc) return rc;
@@ -581,13 +582,15 @@ int extents_of(const sbp_sim *s, int comp, int e[3])
     return SBP_OK;
 }
 
-int create_common(const sbp_grid_desc *d, void *stream, void *ws, size_t bytes, bool own, sbp_sim **out)
+int create_common(const sbp_grid_desc *d, void *stream, void *ws, size_t bytes, bool own, sbp_sim **out,
+                  bool async_setup = false)
 {
     if (!out || !desc_valid(d)) return SBP_EINVAL;
     *out = nullptr;
     Layout L = make_layout(d);
     sbp_sim *s = new (std::nothrow) sbp_sim();
     if (!s) return SBP_ENOMEM;
+    s->async_setup = async_setup;
     cudaGetDevice(&s->device);
     s->stream = static_cast<cudaStream_t>(stream);
     if (own) {
@@ -1258,6 +1261,12 @@ int sbp_batch_destroy(sbp_batch *b)
     return SBP_OK;
 }
 
+}  // extern "C"
+
+#include "server.cuh"
+
+extern "C" {
+
 const char *sbp_strerror(int code)
 {
     switch (code) {
@@ -1270,6 +1279,7 @@ const char *sbp_strerror(int code)
     case SBP_ENOTCONFORMING: return "interface faces do not conform";
     case SBP_ESTATE: return "call not valid in the current state";
     case SBP_ECAPACITY: return "buffer too small";
+    case SBP_EAGAIN: return "not finished yet";
     default: return "unknown error";
     }
 }

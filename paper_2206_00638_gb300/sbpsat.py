@@ -136,7 +136,8 @@ def exported_symbols() -> Sequence[str]:
             "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
             "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
             "sbp_batch_create", "sbp_batch_add", "sbp_batch_remove", "sbp_batch_remaining", "sbp_batch_step",
-            "sbp_batch_size", "sbp_batch_destroy"]
+            "sbp_batch_size", "sbp_batch_destroy", "sbp_server_create", "sbp_server_submit", "sbp_server_poll",
+            "sbp_server_probes", "sbp_server_release", "sbp_server_drain", "sbp_server_stats", "sbp_server_destroy"]
 
 
 def _strerror(code: int) -> str:
@@ -407,6 +408,129 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None):
             lib().sbp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SourceDesc(C.Structure):
+    _fields_ = [("comp", C.c_int32), ("i", C.c_int32), ("j", C.c_int32), ("k", C.c_int32),
+                ("waveform", C.c_int32), ("amp", C.c_double), ("tw", C.c_double), ("t0", C.c_double),
+                ("f", C.c_double)]
+
+
+class ProbeDesc(C.Structure):
+    _fields_ = [("comp", C.c_int32), ("i", C.c_int32), ("j", C.c_int32), ("k", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("grid", GridDesc), ("nsteps", C.c_int64), ("nsources", C.c_int32),
+                ("sources", C.POINTER(SourceDesc)), ("nprobes", C.c_int32), ("probes", C.POINTER(ProbeDesc))]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("steps", C.c_int64), ("submit_s", C.c_double),
+                ("admit_s", C.c_double), ("done_s", C.c_double), ("nprobes", C.c_int32)]
+
+
+_SERVER_SIGS = {
+    "sbp_server_create": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "sbp_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+    "sbp_server_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(Result)]),
+    "sbp_server_probes": (C.c_int, [C.c_void_p, C.c_uint64, C.POINTER(C.c_double), C.c_int64]),
+    "sbp_server_release": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "sbp_server_drain": (C.c_int, [C.c_void_p]),
+    "sbp_server_stats": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "sbp_server_destroy": (C.c_int, [C.c_void_p]),
+}
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_sigs", False):
+        for name, (res, args) in _SERVER_SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        L._server_sigs = True
+    return L
+
+
+class Server:
+    """Request loop with continuous batching (wraps ``sbp_server``).  ``submit`` copies the
+    request; a scheduler thread in the library admits, batches, steps and retires requests."""
+
+    def __init__(self, stream=None, budget_bytes=0, max_slots=64, chunk=32):
+        L = _server_lib()
+        self.stream = _stream_ptr(stream)
+        h = C.c_void_p()
+        _check(L.sbp_server_create(self.stream, int(budget_bytes), int(max_slots), int(chunk), C.byref(h)),
+               "sbp_server_create")
+        self._h = h.value
+        self.meta = {}
+
+    def submit(self, spec, nsteps, cfl=0.95):
+        """spec: workloads.BlockSpec (FP32, uniform mu, >= 8 cells per axis, no interfaces)."""
+        d = GridDesc()
+        d.nx, d.ny, d.nz = spec.n
+        d.dx, d.dy, d.dz = spec.h
+        eps = None
+        if spec.eps_r is not None:
+            eps = np.ascontiguousarray(np.asarray(spec.eps_r, dtype=np.float32).reshape(-1))
+            d.eps_r = eps.ctypes.data_as(C.POINTER(C.c_float))
+        d.mu_r = None
+        for f in range(6):
+            d.face[f] = int(spec.faces[f])
+        d.cfl_fraction = float(cfl)
+        d.precision = FP32
+        d.energy_every = 0
+        d.flags = 0
+        srcs = (SourceDesc * max(len(spec.sources), 1))()
+        for q, s in enumerate(spec.sources):
+            srcs[q] = SourceDesc(s.comp, s.i, s.j, s.k, s.kind, s.amp, s.tw, s.t0, s.f)
+        prbs = (ProbeDesc * max(len(spec.probes), 1))()
+        for q, p in enumerate(spec.probes):
+            prbs[q] = ProbeDesc(p.comp, p.i, p.j, p.k)
+        r = Request(d, int(nsteps), len(spec.sources), srcs, len(spec.probes), prbs)
+        t = C.c_uint64()
+        _check(_server_lib().sbp_server_submit(self._h, C.byref(r), C.byref(t)), "sbp_server_submit")
+        self.meta[t.value] = (len(spec.probes), int(nsteps), int(np.prod(spec.n)))
+        return t.value
+
+    def poll(self, ticket):
+        res = Result()
+        rc = _server_lib().sbp_server_poll(self._h, ticket, C.byref(res))
+        if rc == -9:
+            return None
+        _check(rc, "sbp_server_poll")
+        return res
+
+    def probes(self, ticket):
+        npr, nsteps, _ = self.meta[ticket]
+        out = np.zeros((max(npr, 1), max(nsteps, 1)))
+        _check(_server_lib().sbp_server_probes(self._h, ticket, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                               max(nsteps, 1)), "sbp_server_probes")
+        return out[:npr, :nsteps]
+
+    def release(self, ticket):
+        _check(_server_lib().sbp_server_release(self._h, ticket), "sbp_server_release")
+        self.meta.pop(ticket, None)
+
+    def drain(self):
+        _check(_server_lib().sbp_server_drain(self._h), "sbp_server_drain")
+
+    def stats(self):
+        cu, span = C.c_double(), C.c_double()
+        _check(_server_lib().sbp_server_stats(self._h, C.byref(cu), C.byref(span)), "sbp_server_stats")
+        return cu.value, span.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _server_lib().sbp_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

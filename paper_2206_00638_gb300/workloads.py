@@ -221,3 +221,40 @@ def coupled_boxes(nA, nB, axis: int, h=(1e-3, 1e-3, 1e-3), facesA=(PEC,) * 6, fa
     wa = random_box(nA, h, facesA, seed=seed, cfl=cfl, steps=steps)
     wb = random_box(nB, h, facesB, seed=seed + 1, cfl=cfl, steps=steps, sources=False)
     return Workload(f"coupled_{axis}", wa.blocks + wb.blocks, [(0, 2 * axis + 1, 1, 2 * axis)], cfl, steps)
+
+
+def serving_requests(nreq: int = 512, seed: int = 4, n_range=(32, 192), steps_range=(500, 4000),
+                     eps_range=(1.0, 6.0), sub: int = 16):
+    """Compact descriptors of the serving workload's requests (materialise with serving_spec):
+    per-axis cells ~ U{n_range}, steps ~ U{steps_range}, each face PEC or absorbing with
+    probability 1/2, eps_r ~ U[eps_range] per sub^3-cell sub-box, a 10 GHz Gaussian-derivative
+    Ez dipole at a uniformly random interior node and one Ez probe two nodes above it."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(nreq):
+        n = tuple(int(rng.integers(n_range[0], n_range[1] + 1)) for _ in range(3))
+        faces = tuple(int(PEC if rng.random() < 0.5 else ABSORBING) for _ in range(6))
+        nb = [(n[a] + sub - 1) // sub for a in range(3)]
+        boxes = rng.uniform(*eps_range, size=(nb[2], nb[1], nb[0])).astype(np.float32)
+        e = extents(n, EZ)
+        pos = tuple(int(rng.integers(3, e[a] - 3)) for a in range(3))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        out.append({"n": n, "faces": faces, "boxes": boxes, "sub": sub, "pos": pos, "steps": steps})
+    return out
+
+
+def serving_spec(r, h: float = 1e-3) -> BlockSpec:
+    n, sub, pos = r["n"], r["sub"], r["pos"]
+    eps = np.repeat(np.repeat(np.repeat(r["boxes"], sub, 0), sub, 1), sub, 2)[: n[2], : n[1], : n[0]]
+    tw = gaussian_deriv_tw(10e9)
+    e = extents(n, EZ)
+    return BlockSpec(n=n, h=(h,) * 3, faces=r["faces"], eps_r=np.ascontiguousarray(eps),
+                     sources=[Source(EZ, *pos, GAUSS_DERIV, 1.0, tw, tw)],
+                     probes=[Probe(EZ, pos[0], pos[1], min(pos[2] + 2, e[2] - 1))])
+
+
+def serving_stream(nreq: int = 512, seed: int = 4, n_range=(32, 192), steps_range=(500, 4000),
+                   eps_range=(1.0, 6.0), sub: int = 16, h: float = 1e-3):
+    """The serving workload materialised: a list of (BlockSpec, nsteps)."""
+    return [(serving_spec(r, h), r["steps"])
+            for r in serving_requests(nreq, seed, n_range, steps_range, eps_range, sub)]
