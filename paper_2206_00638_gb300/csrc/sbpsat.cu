@@ -583,9 +583,9 @@ int extents_of(const sbp_sim *s, int comp, int e[3])
 }
 
 int create_common(const sbp_grid_desc *d, void *stream, void *ws, size_t bytes, bool own, sbp_sim **out,
-                  bool async_setup = false)
+                  bool async_setup = false, bool validated = false)
 {
-    if (!out || !desc_valid(d)) return SBP_EINVAL;
+    if (!out || (!validated && !desc_valid(d))) return SBP_EINVAL;
     *out = nullptr;
     Layout L = make_layout(d);
     sbp_sim *s = new (std::nothrow) sbp_sim();
@@ -788,6 +788,10 @@ struct sbp_batch {
     long long *d_counters = nullptr;
     int cap = 0;
     int nf = 0, nh = 0, ne = 0;         // CTAs per launch
+    sbp::BatchGrid *h_grids = nullptr;  // pinned staging of the uploads
+    int *h_pre = nullptr;
+    long long *h_counters = nullptr;
+    cudaEvent_t staged = nullptr;       // the last upload has left the staging buffers
     bool dirty = true;
     bool use_graph = true;
     cudaGraphExec_t gexec = nullptr;
@@ -804,10 +808,18 @@ int batch_reserve(sbp_batch *b, int n)
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_pre) cudaFree(b->d_pre);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->h_grids) cudaFreeHost(b->h_grids);
+    if (b->h_pre) cudaFreeHost(b->h_pre);
+    if (b->h_counters) cudaFreeHost(b->h_counters);
     b->d_grids = nullptr; b->d_pre = nullptr; b->d_counters = nullptr;
+    b->h_grids = nullptr; b->h_pre = nullptr; b->h_counters = nullptr;
     SBP_CUDA(cudaMalloc(&b->d_grids, sizeof(sbp::BatchGrid) * cap));
     SBP_CUDA(cudaMalloc(&b->d_pre, sizeof(int) * 3 * (cap + 1)));
     SBP_CUDA(cudaMalloc(&b->d_counters, sizeof(long long) * cap));
+    SBP_CUDA(cudaHostAlloc((void **)&b->h_grids, sizeof(sbp::BatchGrid) * cap, cudaHostAllocDefault));
+    SBP_CUDA(cudaHostAlloc((void **)&b->h_pre, sizeof(int) * 3 * (cap + 1), cudaHostAllocDefault));
+    SBP_CUDA(cudaHostAlloc((void **)&b->h_counters, sizeof(long long) * cap, cudaHostAllocDefault));
+    if (!b->staged) SBP_CUDA(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
     b->cap = cap;
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
     return SBP_OK;
@@ -819,14 +831,17 @@ int batch_rebuild(sbp_batch *b)
     const int n = (int)b->m.size();
     int rc = batch_reserve(b, std::max(n, 1));
     if (rc) return rc;
-    std::vector<sbp::BatchGrid> hg(std::max(n, 1));
-    std::vector<int> pre(3 * (b->cap + 1), 0);
-    std::vector<long long> cnt(std::max(n, 1), 0);
-    int *pf = pre.data(), *ph = pre.data() + (b->cap + 1), *pe = pre.data() + 2 * (b->cap + 1);
+    // the previous upload must have left the pinned staging buffers
+    SBP_CUDA(cudaEventSynchronize(b->staged));
+    sbp::BatchGrid *hg = b->h_grids;
+    int *pre = b->h_pre;
+    long long *cnt = b->h_counters;
+    std::memset(pre, 0, sizeof(int) * 3 * (b->cap + 1));
+    int *pf = pre, *ph = pre + (b->cap + 1), *pe = pre + 2 * (b->cap + 1);
     for (int g = 0; g < n; g++) {
         sbp_sim *s = b->m[g].s;
         sbp::BatchGrid &G = hg[g];
-        std::memset(&G, 0, sizeof(G));
+        std::memset(static_cast<void *>(&G), 0, sizeof(G));
         for (int c = 0; c < 2; c++) {
             G.maps[c] = s->maps[c];
             if ((rc = make_fused_params(s, c, G.fp[c]))) return rc;
@@ -857,10 +872,11 @@ int batch_rebuild(sbp_batch *b)
     }
     b->nf = pf[n]; b->nh = ph[n]; b->ne = pe[n];
     if (n > 0) {
-        SBP_CUDA(cudaMemcpyAsync(b->d_grids, hg.data(), sizeof(sbp::BatchGrid) * n, cudaMemcpyHostToDevice, b->stream));
-        SBP_CUDA(cudaMemcpyAsync(b->d_pre, pre.data(), sizeof(int) * pre.size(), cudaMemcpyHostToDevice, b->stream));
-        SBP_CUDA(cudaMemcpyAsync(b->d_counters, cnt.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));
-        SBP_CUDA(cudaStreamSynchronize(b->stream));   // host staging buffers are released on return
+        // stream-ordered behind the chunks already queued, which read the old tables
+        SBP_CUDA(cudaMemcpyAsync(b->d_grids, hg, sizeof(sbp::BatchGrid) * n, cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaMemcpyAsync(b->d_pre, pre, sizeof(int) * 3 * (b->cap + 1), cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaMemcpyAsync(b->d_counters, cnt, sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaEventRecord(b->staged, b->stream));
     }
     if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
     b->dirty = false;
@@ -1257,6 +1273,10 @@ int sbp_batch_destroy(sbp_batch *b)
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_pre) cudaFree(b->d_pre);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->h_grids) cudaFreeHost(b->h_grids);
+    if (b->h_pre) cudaFreeHost(b->h_pre);
+    if (b->h_counters) cudaFreeHost(b->h_counters);
+    if (b->staged) cudaEventDestroy(b->staged);
     delete b;
     return SBP_OK;
 }

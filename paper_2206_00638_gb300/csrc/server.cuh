@@ -3,9 +3,12 @@
 // One scheduler thread per server owns every device call: it admits
 // requests in arrival order while a slot and enough of the HBM budget are
 // free (device memory comes from the stream-ordered pool, so neither
-// allocation nor release synchronises the device), lets admitted requests
-// join the running sbp_batch at the next chunk boundary, advances the batch
-// one graph-captured chunk at a time (at most two chunks in flight), and
+// allocation nor release synchronises the device; set-up runs on a separate
+// admission stream joined to the batch stream by an event), lets admitted
+// requests join the running sbp_batch at the next chunk boundary, advances
+// the batch one chunk at a time (at most two chunks in flight; a batched
+// step covers every member in three launches, so launch overhead is already
+// amortised and no graph is re-instantiated on membership changes), and
 // retires finished requests: their probe samples are copied to pinned host
 // memory behind an event and their memory goes back to the pool.
 #include <chrono>
@@ -59,6 +62,7 @@ void destroy_sim_async(sbp_sim *s)
 
 struct sbp_server {
     cudaStream_t stream = nullptr;
+    cudaStream_t adm = nullptr;           // admissions: allocation, material upload, set-up kernels
     int device = 0;
     size_t budget = 0, used = 0;
     int max_slots = 1, chunk = 32;
@@ -88,13 +92,15 @@ void finish(sbp_server *S, const std::shared_ptr<ServerRequest> &r, int status)
     S->cv_done.notify_all();
 }
 
-// Create the request's simulation on the server stream (asynchronous setup).
+// Create the request's simulation on the admission stream (its pageable
+// material upload waits only for that stream), then hand it to the batch
+// stream, which waits for the set-up to finish before the next chunk.
 int admit(sbp_server *S, const std::shared_ptr<ServerRequest> &r)
 {
-    cudaError_t e = cudaMallocAsync(&r->ws, r->ws_bytes, S->stream);
+    cudaError_t e = cudaMallocAsync(&r->ws, r->ws_bytes, S->adm);
     if (e != cudaSuccess) { (void)cudaGetLastError(); r->ws = nullptr; return cuda_fail(e); }
     sbp_sim *s = nullptr;
-    int rc = create_common(&r->desc, S->stream, r->ws, r->ws_bytes, false, &s, true);
+    int rc = create_common(&r->desc, S->adm, r->ws, r->ws_bytes, false, &s, true, true);
     if (rc) return rc;
     r->sim = s;
     for (const auto &q : r->src) {
@@ -106,13 +112,19 @@ int admit(sbp_server *S, const std::shared_ptr<ServerRequest> &r)
         if ((rc = sbp_add_probe(s, q.comp, q.i, q.j, q.k, &id))) return rc;
     }
     if (r->probe_bytes) {
-        e = cudaMallocAsync(&r->probe_dev, r->probe_bytes, S->stream);
+        e = cudaMallocAsync(&r->probe_dev, r->probe_bytes, S->adm);
         if (e != cudaSuccess) { (void)cudaGetLastError(); r->probe_dev = nullptr; return cuda_fail(e); }
-        SBP_CUDA(cudaMemsetAsync(r->probe_dev, 0, r->probe_bytes, S->stream));
+        SBP_CUDA(cudaMemsetAsync(r->probe_dev, 0, r->probe_bytes, S->adm));
         s->probe_buf = r->probe_dev;
         s->probe_cap = r->nsteps;
         s->probe_base = s->step;
     }
+    cudaEvent_t ready;
+    SBP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    SBP_CUDA(cudaEventRecord(ready, S->adm));
+    SBP_CUDA(cudaStreamWaitEvent(S->stream, ready, 0));
+    cudaEventDestroy(ready);
+    s->stream = S->stream;
     return sbp_batch_add(S->batch, s, r->nsteps);
 }
 
@@ -239,8 +251,14 @@ int sbp_server_create(void *cuda_stream, size_t hbm_budget_bytes, int max_slots,
     S->budget = hbm_budget_bytes ? std::min(hbm_budget_bytes, cap) : cap;
     S->max_slots = max_slots;
     S->chunk = chunk_steps;
-    int rc = sbp_batch_create(cuda_stream, 1, &S->batch);
+    int rc = sbp_batch_create(cuda_stream, 0, &S->batch);
     if (rc) { delete S; return rc; }
+    if (cudaStreamCreateWithFlags(&S->adm, cudaStreamNonBlocking) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sbp_batch_destroy(S->batch);
+        delete S;
+        return SBP_ECUDA;
+    }
     S->worker = std::thread(server_loop, S);
     *out = S;
     return SBP_OK;
@@ -360,6 +378,8 @@ int sbp_server_destroy(sbp_server *S)
     for (auto &kv : S->all)
         if (kv.second->probe_host) cudaFreeHost(kv.second->probe_host);
     cudaStreamSynchronize(S->stream);
+    cudaStreamSynchronize(S->adm);
+    cudaStreamDestroy(S->adm);
     sbp_batch_destroy(S->batch);
     delete S;
     return SBP_OK;
