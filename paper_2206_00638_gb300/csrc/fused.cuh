@@ -377,38 +377,33 @@ __device__ __forceinline__ void band_node(const Band &b, const int n[3], long lo
     i = (int)xr < lo ? (int)xr : b.hi[0] + 1 + ((int)xr - lo);
 }
 
-// H^{n+1/2} of component 3+c at band node t: p.F = {E^n (old), H^{n-1/2}
-// (old)}, outs = new H.  One thread per (node, component): three times the
-// parallelism of one thread per node and a third of its dependent loads.
+// H^{n+1/2} at band node t: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
 template <typename T, bool MUVAR>
 __device__ __forceinline__ void band_h_node(const Params<T> &p, const Band &b, long long t, long long pslot,
-                                            T *const outs[3], int c)
+                                            T *const outs[3])
 {
     int i, j, k;
     band_node(b, p.n, t, i, j, k);
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int idx[3] = {i, j, k};
     const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
-    T hn;
-    if (c == 0) {
-        if (!(i <= nx && j <= ny + 1 && k <= nz + 1)) return;
-        hn = h_node<T, 3, MUVAR>(p, idx, o, p.F[3][o]);
-    } else if (c == 1) {
-        if (!(i <= nx + 1 && j <= ny && k <= nz + 1)) return;
-        hn = h_node<T, 4, MUVAR>(p, idx, o, p.F[4][o]);
-    } else {
-        if (!(i <= nx + 1 && j <= ny + 1 && k <= nz)) return;
-        hn = h_node<T, 5, MUVAR>(p, idx, o, p.F[5][o]);
-    }
-    outs[c][o] = hn;
-    for (int q = 0; q < p.nprb; ++q) {
-        const Prb &P = p.prb[q];
-        if (P.comp == 3 + c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
-            p.probe_buf[(long long)q * p.probe_cap + pslot] = hn;
+    T hn[3];
+    bool have[3] = {i <= nx && j <= ny + 1 && k <= nz + 1, i <= nx + 1 && j <= ny && k <= nz + 1,
+                    i <= nx + 1 && j <= ny + 1 && k <= nz};
+    if (have[0]) hn[0] = h_node<T, 3, MUVAR>(p, idx, o, p.F[3][o]);
+    if (have[1]) hn[1] = h_node<T, 4, MUVAR>(p, idx, o, p.F[4][o]);
+    if (have[2]) hn[2] = h_node<T, 5, MUVAR>(p, idx, o, p.F[5][o]);
+    for (int c = 0; c < 3; ++c) {
+        if (!have[c]) continue;
+        outs[c][o] = hn[c];
+        for (int q = 0; q < p.nprb; ++q) {
+            const Prb &P = p.prb[q];
+            if (P.comp == 3 + c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
+                p.probe_buf[(long long)q * p.probe_cap + pslot] = hn[c];
+        }
     }
 }
 
-// grid: x covers the band nodes, y = the component (0..2)
 template <typename T, bool MUVAR>
 __global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T *hx_out, T *hy_out, T *hz_out)
 {
@@ -416,14 +411,13 @@ __global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= total) return;
     T *const outs[3] = {hx_out, hy_out, hz_out};
-    band_h_node<T, MUVAR>(p, b, t, p.probe_slot, outs, blockIdx.y);
+    band_h_node<T, MUVAR>(p, b, t, p.probe_slot, outs);
 }
 
-// E^{n+1} of component c at band node t: p.F = {E^n (old), H^{n+1/2} (new)},
-// outs = new E.  One thread per (node, component).
+// E^{n+1} at band node t: p.F = {E^n (old), H^{n+1/2} (new)}, outs = new E.
 template <typename T, bool MUVAR>
 __device__ __forceinline__ void band_e_node(const Params<T> &p, const Band &b, long long t, long long step,
-                                            long long pslot, T *const outs[3], int c)
+                                            long long pslot, T *const outs[3])
 {
     int i, j, k;
     band_node(b, p.n, t, i, j, k);
@@ -432,25 +426,22 @@ __device__ __forceinline__ void band_e_node(const Params<T> &p, const Band &b, l
     const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
     unsigned sm = 0u;
     for (int q = 0; q < p.nsrc; ++q)
-        if (p.src[q].comp == c && (p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j))
-            sm |= 1u << q;
+        if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) sm |= 1u << q;
     const double t_half = ((double)step + 0.5) * p.dt;
-    T en;
-    if (c == 0) {
-        if (!(i <= nx + 1 && j <= ny && k <= nz)) return;
-        en = e_node<T, 0, MUVAR>(p, idx, o, p.F[0][o], sm, t_half);
-    } else if (c == 1) {
-        if (!(i <= nx && j <= ny + 1 && k <= nz)) return;
-        en = e_node<T, 1, MUVAR>(p, idx, o, p.F[1][o], sm, t_half);
-    } else {
-        if (!(i <= nx && j <= ny && k <= nz + 1)) return;
-        en = e_node<T, 2, MUVAR>(p, idx, o, p.F[2][o], sm, t_half);
-    }
-    outs[c][o] = en;
-    for (int q = 0; q < p.nprb; ++q) {
-        const Prb &P = p.prb[q];
-        if (P.comp == c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
-            p.probe_buf[(long long)q * p.probe_cap + pslot] = en;
+    T en[3];
+    bool have[3] = {i <= nx + 1 && j <= ny && k <= nz, i <= nx && j <= ny + 1 && k <= nz,
+                    i <= nx && j <= ny && k <= nz + 1};
+    if (have[0]) en[0] = e_node<T, 0, MUVAR>(p, idx, o, p.F[0][o], sm, t_half);
+    if (have[1]) en[1] = e_node<T, 1, MUVAR>(p, idx, o, p.F[1][o], sm, t_half);
+    if (have[2]) en[2] = e_node<T, 2, MUVAR>(p, idx, o, p.F[2][o], sm, t_half);
+    for (int c = 0; c < 3; ++c) {
+        if (!have[c]) continue;
+        outs[c][o] = en[c];
+        for (int q = 0; q < p.nprb; ++q) {
+            const Prb &P = p.prb[q];
+            if (P.comp == c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
+                p.probe_buf[(long long)q * p.probe_cap + pslot] = en[c];
+        }
     }
 }
 
@@ -461,7 +452,7 @@ __global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (t >= total) return;
     T *const outs[3] = {ex_out, ey_out, ez_out};
-    band_e_node<T, MUVAR>(p, b, t, p.step, p.probe_slot, outs, blockIdx.y);
+    band_e_node<T, MUVAR>(p, b, t, p.step, p.probe_slot, outs);
 }
 
 // ---------------------------------------------------------------------------
@@ -531,7 +522,7 @@ __global__ void __launch_bounds__(256) band_h_batched(const BatchGrid *G, const 
     if (!batch_state(B, offset, step, par)) return;
     const long long t = (long long)(blockIdx.x - pre[g]) * blockDim.x + threadIdx.x;
     if (t >= B.bh.nz_slab + B.bh.ny_slab + B.bh.nx_slab) return;
-    band_h_node<float, false>(B.ph[par], B.bh, t, step - B.probe_base, B.hout[par], blockIdx.y);
+    band_h_node<float, false>(B.ph[par], B.bh, t, step - B.probe_base, B.hout[par]);
 }
 
 __global__ void __launch_bounds__(256) band_e_batched(const BatchGrid *G, const int *pre, int n, int offset)
@@ -543,7 +534,7 @@ __global__ void __launch_bounds__(256) band_e_batched(const BatchGrid *G, const 
     if (!batch_state(B, offset, step, par)) return;
     const long long t = (long long)(blockIdx.x - pre[g]) * blockDim.x + threadIdx.x;
     if (t >= B.be.nz_slab + B.be.ny_slab + B.be.nx_slab) return;
-    band_e_node<float, false>(B.pe[par], B.be, t, step, step - B.probe_base, B.eout[par], blockIdx.y);
+    band_e_node<float, false>(B.pe[par], B.be, t, step, step - B.probe_base, B.eout[par]);
 }
 
 __global__ void batch_advance(const BatchGrid *G, int n, long long k)

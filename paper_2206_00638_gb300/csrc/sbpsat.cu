@@ -482,7 +482,7 @@ int launch_fused_phase1(sbp_sim *s)
     float **ns = reinterpret_cast<float **>(s->set[nw]);
     SBP_CUDA(cudaEventRecord(s->ev_fork, s->stream));
     SBP_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-    sbp::band_h<float, false><<<dim3((unsigned)((tot + 255) / 256), 3), 256, 0, s->side>>>(p, bh, ns[3], ns[4], ns[5]);
+    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->side>>>(p, bh, ns[3], ns[4], ns[5]);
     SBP_CUDA(cudaGetLastError());
     SBP_CUDA(cudaEventRecord(s->ev_join, s->side));
     rc = launch_fused_interior_only(s);
@@ -501,7 +501,7 @@ int launch_fused_phase2(sbp_sim *s)
     const sbp::Band &be = s->band_eb;
     const long long tot = be.nz_slab + be.ny_slab + be.nx_slab;
     float **ns = reinterpret_cast<float **>(s->set[nw]);
-    sbp::band_e<float, false><<<dim3((unsigned)((tot + 255) / 256), 3), 256, 0, s->stream>>>(p, be, ns[0], ns[1], ns[2]);
+    sbp::band_e<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, be, ns[0], ns[1], ns[2]);
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
 }
@@ -726,7 +726,7 @@ int step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, in
             const long long tot_h = bh.nz_slab + bh.ny_slab + bh.nx_slab;
             float **ns = reinterpret_cast<float **>(s->set[nw]);
             if ((rc = mark(2))) break;
-            sbp::band_h<float, false><<<dim3((unsigned)((tot_h + 255) / 256), 3), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+            sbp::band_h<float, false><<<(unsigned)((tot_h + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
             if ((rc = mark(-1))) break;
             // fused_interior alone: reuse phase 1 with the band launch skipped
             if ((rc = mark(3))) break;
@@ -889,10 +889,10 @@ int batch_launch_chunk(sbp_batch *b, long long K)
     const int n = (int)b->m.size();
     const int *pf = b->d_pre, *ph = b->d_pre + (b->cap + 1), *pe = b->d_pre + 2 * (b->cap + 1);
     for (long long o = 0; o < K; o++) {
-        if (b->nh > 0) sbp::band_h_batched<<<dim3(b->nh, 3), 256, 0, b->stream>>>(b->d_grids, ph, n, (int)o);
+        if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->stream>>>(b->d_grids, ph, n, (int)o);
         if (b->nf > 0)
             sbp::fused_batched<<<b->nf, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(b->d_grids, pf, n, (int)o);
-        if (b->ne > 0) sbp::band_e_batched<<<dim3(b->ne, 3), 256, 0, b->stream>>>(b->d_grids, pe, n, (int)o);
+        if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->stream>>>(b->d_grids, pe, n, (int)o);
     }
     sbp::batch_advance<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_grids, n, K);
     SBP_CUDA(cudaGetLastError());
