@@ -57,13 +57,6 @@ struct FusedParams {
     long long probe_cap, probe_slot, step;
     int kchunk;
     int *error_flag;                     // set to 1 when a pipeline wait gives up
-    // x/y boundary layers inside the sweep: tiles start at x = bx*wx, y = by*wy
-    // and cover every node of those axes; nodes in the three boundary layers
-    // of x or y take the general path of kernels.cuh reading global memory
-    // (gh: the old set; ge: E old, H new), which needs edge tiles to store
-    // every H^{n+1/2} they compute (halos included: equal to the owner's).
-    int xy, wx, wy;
-    const Params<float> *gh, *ge;
 };
 
 // --- mbarrier / TMA helpers (inline PTX) ----------------------------------
@@ -131,13 +124,11 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
-    const bool xy = p.xy != 0;
-    const int wx = xy ? p.wx : kFTX - 1, wy = xy ? p.wy : kFTY - 1;
-    const int x0 = xy ? bx * wx : 3 + bx * (kFTX - 1);
-    const int y0 = xy ? by * wy : 3 + by * (kFTY - 1);
+    const int x0 = 3 + bx * (kFTX - 1);
+    const int y0 = 3 + by * (kFTY - 1);
     const int k0 = 3 + bz * p.kchunk;
     const int k1 = min(k0 + p.kchunk, nz - 2);       // E planes [k0, k1); H planes [k0, k1]
-    const int xb = (x0 - 1) & ~3;                     // may be -4: loads fill zeros
+    const int xb = (x0 - 1) & ~3;
     const int cx0 = x0 - xb;                          // smem column of x0, in 1..4
     const int nplanes = k1 - k0 + 2;                  // planes k0-1 .. k1 are loaded
     const int j = y0 + w;
@@ -164,39 +155,18 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             for (int q = 0; q < p.nsrc; ++q)
                 if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) smask[h] |= 1u << q;
     }
-    // per column: which components exist here (Table I extents), which stores
-    // this thread makes, whether the node takes the general path, and the
+    const bool rowE = w < kFTY - 1 && j <= ny - 3;
+    const bool rowH = j <= ny - 2 && (w < kFTY - 1 || j == ny - 2);
+    // per column: stores owned (H) / produced (E) by this thread, and the
     // column's offset within a plane
-    bool colH[2], colE[2], genH[2], genE[2];
-    unsigned vH[2], vE[2];                            // bit c: component c exists at (i, j)
+    bool colH[2], colE[2];
     long long obase[2];
-    bool edge = false;
-    if (xy) {
-        const int xe = min(x0 + wx - 1, nx + 1), ye = min(y0 + wy - 1, ny + 1);
-        edge = x0 <= 2 || xe >= nx - 2 || y0 <= 2 || ye >= ny - 2;
-    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int c = lane + 32 * h, i = x0 + c;
+        colH[h] = rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2);
+        colE[h] = rowE && c < kFTX - 1 && i <= nx - 3;
         obase[h] = (long long)j * p.sy + i;
-        if (!xy) {
-            const bool rowE = w < kFTY - 1 && j <= ny - 3;
-            const bool rowH = j <= ny - 2 && (w < kFTY - 1 || j == ny - 2);
-            colH[h] = rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2);
-            colE[h] = rowE && c < kFTX - 1 && i <= nx - 3;
-            genH[h] = genE[h] = false;
-            vH[h] = vE[h] = 7u;
-        } else {
-            vH[h] = (i <= nx && j <= ny + 1 ? 1u : 0u) | (i <= nx + 1 && j <= ny ? 2u : 0u) |
-                    (i <= nx + 1 && j <= ny + 1 ? 4u : 0u);
-            vE[h] = (i <= nx + 1 && j <= ny ? 1u : 0u) | (i <= nx && j <= ny + 1 ? 2u : 0u) |
-                    (i <= nx && j <= ny ? 4u : 0u);
-            const bool own = c < wx && w < wy;
-            colH[h] = vH[h] != 0 && (own || edge);
-            colE[h] = vE[h] != 0 && own;
-            genH[h] = i < 3 || i > nx - 2 || j < 3 || j > ny - 2;
-            genE[h] = i < 3 || i > nx - 3 || j < 3 || j > ny - 3;
-        }
     }
     const Coef<float> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
     const Coef<float> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
@@ -243,31 +213,21 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             const float exq = Sq[0 * kEField + re], ex_jm = Sq[0 * kEField + re - kFBX];
             const float eyq = Sq[1 * kEField + re], ey_im = Sq[1 * kEField + re - 1];
             const float ezq = Sq[2 * kEField + re], ez_im = Sq[2 * kEField + re - 1], ez_jm = Sq[2 * kEField + re - kFBX];
-            float hx, hy, hz;
-            if (genH[h]) {
-                // x / y boundary layer: closure rows and SATs (global reads of the old set)
-                const int idx[3] = {x0 + c, j, q};
-                const long long o = (long long)q * p.sz + obase[h];
-                hx = (vH[h] & 1u) ? h_node<float, 3, false>(*p.gh, idx, o, Sq[3 * kEField + 0 * kHField + rh]) : 0.f;
-                hy = (vH[h] & 2u) ? h_node<float, 4, false>(*p.gh, idx, o, Sq[3 * kEField + 1 * kHField + rh]) : 0.f;
-                hz = (vH[h] & 4u) ? h_node<float, 5, false>(*p.gh, idx, o, Sq[3 * kEField + 2 * kHField + rh]) : 0.f;
-            } else {
-                Acc<float> bx, by, bz;
-                bx.add(Bz, eyq - ec[h][1]); bx.add(By, ezq - ez_jm, -1.f);
-                by.add(Bx, ezq - ez_im);    by.add(Bz, exq - ec[h][0], -1.f);
-                bz.add(By, exq - ex_jm);    bz.add(Bx, eyq - ey_im, -1.f);
-                hx = Sq[3 * kEField + 0 * kHField + rh] + plain_increment(bx);
-                hy = Sq[3 * kEField + 1 * kHField + rh] + plain_increment(by);
-                hz = Sq[3 * kEField + 2 * kHField + rh] + plain_increment(bz);
-            }
+            Acc<float> bx, by, bz;
+            bx.add(Bz, eyq - ec[h][1]); bx.add(By, ezq - ez_jm, -1.f);
+            by.add(Bx, ezq - ez_im);    by.add(Bz, exq - ec[h][0], -1.f);
+            bz.add(By, exq - ex_jm);    bz.add(Bx, eyq - ey_im, -1.f);
+            const float hx = Sq[3 * kEField + 0 * kHField + rh] + plain_increment(bx);
+            const float hy = Sq[3 * kEField + 1 * kHField + rh] + plain_increment(by);
+            const float hz = Sq[3 * kEField + 2 * kHField + rh] + plain_increment(bz);
             Hq[(0 * kFTY + w) * kFTX + c] = hx;
             Hq[(1 * kFTY + w) * kFTX + c] = hy;
             Hq[(2 * kFTY + w) * kFTX + c] = hz;
-            if (colH[h] && (q < k1 || q == nz - 2 || edge)) {
+            if (colH[h] && (q < k1 || q == nz - 2)) {
                 const long long o = (long long)q * p.sz + obase[h];
-                if (vH[h] & 1u) p.out[3][o] = hx;
-                if (vH[h] & 2u) p.out[4][o] = hy;
-                if (vH[h] & 4u) p.out[5][o] = hz;
+                p.out[3][o] = hx;
+                p.out[4][o] = hy;
+                p.out[5][o] = hz;
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
@@ -288,28 +248,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
 
             // ---- E^{n+1} at (i, j, q-1): neighbours' H of plane q-1 from shared
             // memory (written last iteration), own H of planes q-1, q from registers
-            if (doE && colE[h] && genE[h]) {
-                // x / y boundary layer: closure rows, SATs and sources (H^{n+1/2}
-                // read back through L2: stored by this CTA before the barrier)
-                const int idx[3] = {x0 + c, j, pl};
-                const long long o = (long long)pl * p.sz + obase[h];
-                const float ex = (vE[h] & 1u) ? e_node<float, 0, false, true>(*p.ge, idx, o, ec[h][0], smask[h], t_half) : 0.f;
-                const float ey = (vE[h] & 2u) ? e_node<float, 1, false, true>(*p.ge, idx, o, ec[h][1], smask[h], t_half) : 0.f;
-                const float ez = (vE[h] & 4u) ? e_node<float, 2, false, true>(*p.ge, idx, o, ec[h][2], smask[h], t_half) : 0.f;
-                if (vE[h] & 1u) p.out[0][o] = ex;
-                if (vE[h] & 2u) p.out[1][o] = ey;
-                if (vE[h] & 4u) p.out[2][o] = ez;
-                if (pmask[h]) {
-                    unsigned long long m = pmask[h];
-                    while (m) {
-                        const int b = __ffsll(m) - 1;
-                        m &= m - 1;
-                        const Prb &P = p.prb[b];
-                        if (P.k == pl && P.comp < 3 && pslot < p.probe_cap)
-                            p.probe_buf[(long long)b * p.probe_cap + pslot] = P.comp == 0 ? ex : P.comp == 1 ? ey : ez;
-                    }
-                }
-            } else if (doE && colE[h]) {
+            if (doE && colE[h]) {
                 const float hx_jp = Hp[(0 * kFTY + w + 1) * kFTX + c];
                 const float hy_ip = Hp[(1 * kFTY + w) * kFTX + c + 1];
                 const float hz_ip = Hp[(2 * kFTY + w) * kFTX + c + 1];
@@ -393,7 +332,7 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
 // then full y-rows of the remaining planes, then the x-ends of what is left.
 // ---------------------------------------------------------------------------
 struct Band {
-    int lo[3];               // interior box lower bound per axis (inclusive)
+    int lo;
     int hi[3];               // interior box upper bound per axis (inclusive)
     long long nz_slab, ny_slab, nx_slab;   // node counts of the three slabs
 };
@@ -403,38 +342,39 @@ __device__ __forceinline__ void band_node(const Band &b, const int n[3], long lo
     // 32-bit index arithmetic: every slab of a grid this library accepts has
     // fewer than 2^32 nodes (the host checks), and 64-bit division is slow.
     const unsigned ex = n[0] + 2, ey = n[1] + 2;
+    const int lo = b.lo;
     unsigned t = (unsigned)tl;
     if (tl < b.nz_slab) {
         const unsigned plane = t / (ex * ey);
         const unsigned r = t - plane * (ex * ey);
-        k = (int)plane < b.lo[2] ? (int)plane : b.hi[2] + 1 + ((int)plane - b.lo[2]);
+        k = (int)plane < lo ? (int)plane : b.hi[2] + 1 + ((int)plane - lo);
         j = (int)(r / ex);
         i = (int)(r - (unsigned)j * ex);
         return;
     }
     t = (unsigned)(tl - b.nz_slab);
-    const unsigned nyr = b.lo[1] + (n[1] + 1 - b.hi[1]);   // rows below lo and above hi
+    const unsigned nyr = lo + (n[1] + 1 - b.hi[1]);   // rows below lo and above hi
     if (tl - b.nz_slab < b.ny_slab) {
         const unsigned per_k = nyr * ex;
         const unsigned kk = t / per_k;
         const unsigned r = t - kk * per_k;
         const unsigned yr = r / ex;
-        k = b.lo[2] + (int)kk;
-        j = (int)yr < b.lo[1] ? (int)yr : b.hi[1] + 1 + ((int)yr - b.lo[1]);
+        k = lo + (int)kk;
+        j = (int)yr < lo ? (int)yr : b.hi[1] + 1 + ((int)yr - lo);
         i = (int)(r - yr * ex);
         return;
     }
     t = (unsigned)(tl - b.nz_slab - b.ny_slab);
-    const unsigned nxr = b.lo[0] + (n[0] + 1 - b.hi[0]);
-    const unsigned nyin = b.hi[1] - b.lo[1] + 1;
+    const unsigned nxr = lo + (n[0] + 1 - b.hi[0]);
+    const unsigned nyin = b.hi[1] - lo + 1;
     const unsigned per_k = nyin * nxr;
     const unsigned kk = t / per_k;
     const unsigned r = t - kk * per_k;
     const unsigned yy = r / nxr;
     const unsigned xr = r - yy * nxr;
-    k = b.lo[2] + (int)kk;
-    j = b.lo[1] + (int)yy;
-    i = (int)xr < b.lo[0] ? (int)xr : b.hi[0] + 1 + ((int)xr - b.lo[0]);
+    k = lo + (int)kk;
+    j = lo + (int)yy;
+    i = (int)xr < lo ? (int)xr : b.hi[0] + 1 + ((int)xr - lo);
 }
 
 // H^{n+1/2} at band node t: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.

@@ -64,9 +64,6 @@ struct sbp_sim {
     sbp::FusedMaps maps[2];               // TMA tensor maps reading set 0 / set 1
     int fused_kchunk = 32;
     dim3 fused_grid;
-    int fused_xy = 0, fused_wx = 63, fused_wy = 7;   // x/y boundary layers inside the fused sweep
-    sbp::Params<float> *d_gen = nullptr;  // device: general-path parameters {H old c=0,1; E old/H new c=0,1}
-    bool gen_dirty = true;
     bool async_setup = false;             // caller keeps host inputs alive: no stream syncs in setup
     cudaStream_t side = nullptr;          // band_h runs here, concurrently with fused_interior
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -102,6 +99,8 @@ struct Layout {
     int kchunk;
     dim3 grid;
     bool fused;
+    int fused_kchunk;
+    dim3 fused_grid;
     size_t total;
 };
 
@@ -152,6 +151,19 @@ Layout make_layout(const sbp_grid_desc *d)
     L.partial_bytes = round_up((size_t)L.npartials * sizeof(double), 256);
     L.fused = d->precision == SBP_FP32 && !d->mu_r && d->nx >= 8 && d->ny >= 8 && d->nz >= 8 &&
               !std::getenv("SBP_NO_FUSED");
+    if (L.fused) {
+        const int tx = (d->nx - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
+        const int ty = (d->ny - 5 + sbp::kFTY - 2) / (sbp::kFTY - 1);
+        const long long target = 4ll * 2 * 152;        // about four waves of two CTAs per SM
+        const long long chunks = std::max(1ll, (target + (long long)tx * ty - 1) / ((long long)tx * ty));
+        int kcf = (int)std::max(8ll, ((long long)(d->nz - 5) + chunks - 1) / chunks);
+        if (const char *env = std::getenv("SBP_FUSED_KCHUNK")) {
+            const int v = std::atoi(env);
+            if (v > 0) kcf = v;
+        }
+        L.fused_kchunk = kcf;
+        L.fused_grid = dim3(tx, ty, (d->nz - 5 + kcf - 1) / kcf);
+    }
     L.total = (L.fused ? 12 : 6) * L.field_bytes + L.cell_bytes * (d->mu_r ? 2 : 1) + L.partial_bytes + 256 + 256;
     return L;
 }
@@ -223,64 +235,6 @@ int encode_maps(sbp_sim *s)
     return SBP_OK;
 }
 
-// Tiling of the fused sweep and the band kernels' slabs, from the cell counts
-// and the face types (called at set-up and when an interface is joined).
-// x/y mode (boundary layers of x and y inside the sweep) needs plain x/y
-// faces and tile strides with n % w != 0, so that every closure row of D+
-// finds its H neighbours inside one tile.
-int configure_fused(sbp_sim *s)
-{
-    const int nx = s->n[0], ny = s->n[1], nz = s->n[2];
-    int wx = 0, wy = 0;
-    bool xy = !std::getenv("SBP_NO_FUSED_XY");
-    for (int f = 0; f < 4; f++)
-        if (s->face[f] == SBP_INTERFACE) xy = false;
-    if (xy) {
-        for (int c : {63, 62, 61})
-            if (nx % c) { wx = c; break; }
-        for (int c : {7, 6, 5})
-            if (ny % c) { wy = c; break; }
-        xy = wx && wy;
-    }
-    int tx, ty;
-    if (xy) {
-        tx = (nx + 2 + wx - 1) / wx;
-        ty = (ny + 2 + wy - 1) / wy;
-    } else {
-        tx = (nx - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
-        ty = (ny - 5 + sbp::kFTY - 2) / (sbp::kFTY - 1);
-    }
-    const long long target = 4ll * 2 * 152;        // about four waves of two CTAs per SM
-    const long long chunks = std::max(1ll, (target + (long long)tx * ty - 1) / ((long long)tx * ty));
-    int kcf = (int)std::max(8ll, ((long long)(nz - 5) + chunks - 1) / chunks);
-    if (const char *env = std::getenv("SBP_FUSED_KCHUNK")) {
-        const int v = std::atoi(env);
-        if (v > 0) kcf = v;
-    }
-    s->fused_xy = xy ? 1 : 0;
-    s->fused_wx = xy ? wx : sbp::kFTX - 1;
-    s->fused_wy = xy ? wy : sbp::kFTY - 1;
-    s->fused_kchunk = kcf;
-    s->fused_grid = dim3(tx, ty, (nz - 5 + kcf - 1) / kcf);
-    for (int phase = 0; phase < 2; phase++) {
-        sbp::Band &b = phase == 0 ? s->band_hb : s->band_eb;
-        const int d = phase == 0 ? 2 : 3;              // interior box [3, n-2] for H, [3, n-3] for E
-        b.lo[0] = xy ? 0 : 3;
-        b.lo[1] = xy ? 0 : 3;
-        b.lo[2] = 3;
-        b.hi[0] = xy ? nx + 1 : nx - d;
-        b.hi[1] = xy ? ny + 1 : ny - d;
-        b.hi[2] = nz - d;
-        const long long ex = nx + 2, ey = ny + 2;
-        b.nz_slab = (long long)(b.lo[2] + (nz + 1 - b.hi[2])) * ex * ey;
-        b.ny_slab = (long long)(b.hi[2] - b.lo[2] + 1) * (b.lo[1] + (ny + 1 - b.hi[1])) * ex;
-        b.nx_slab = (long long)(b.hi[2] - b.lo[2] + 1) * (b.hi[1] - b.lo[1] + 1) * (b.lo[0] + (nx + 1 - b.hi[0]));
-        if (b.nz_slab >= (1ll << 32) || b.ny_slab >= (1ll << 32) || b.nx_slab >= (1ll << 32)) return SBP_EINVAL;
-    }
-    s->gen_dirty = true;
-    return SBP_OK;
-}
-
 int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
 {
     s->prec = d->precision;
@@ -297,6 +251,8 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     s->grid = L.grid;
     s->npartials = L.npartials;
     s->fused_ok = L.fused;
+    s->fused_kchunk = L.fused_kchunk;
+    s->fused_grid = L.fused_grid;
     char *p = ws;
     for (int set = 0; set < (L.fused ? 2 : 1); set++)
         for (int c = 0; c < 6; c++) { s->set[set][c] = p; p += L.field_bytes; }
@@ -335,7 +291,16 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
         SBP_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
         SBP_CUDA(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
         SBP_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
-        if ((rc = configure_fused(s))) return rc;
+        for (int phase = 0; phase < 2; phase++) {
+            sbp::Band &b = phase == 0 ? s->band_hb : s->band_eb;
+            b.lo = 3;
+            for (int a = 0; a < 3; a++) b.hi[a] = s->n[a] - (phase == 0 ? 2 : 3);
+            const long long ex = s->n[0] + 2, ey = s->n[1] + 2;
+            b.nz_slab = (long long)(b.lo + (s->n[2] + 1 - b.hi[2])) * ex * ey;
+            b.ny_slab = (long long)(b.hi[2] - b.lo + 1) * (b.lo + (s->n[1] + 1 - b.hi[1])) * ex;
+            b.nx_slab = (long long)(b.hi[2] - b.lo + 1) * (b.hi[1] - b.lo + 1) * (b.lo + (s->n[0] + 1 - b.hi[0]));
+            if (b.nz_slab >= (1ll << 32) || b.ny_slab >= (1ll << 32) || b.nx_slab >= (1ll << 32)) return SBP_EINVAL;
+        }
     }
     return SBP_OK;
 }
@@ -470,28 +435,6 @@ int make_fused_params(const sbp_sim *s, int old, sbp::FusedParams &fp)
     fp.step = p.step;
     fp.kchunk = s->fused_kchunk;
     fp.error_flag = s->error_flag;
-    fp.xy = s->fused_xy;
-    fp.wx = s->fused_wx;
-    fp.wy = s->fused_wy;
-    fp.gh = s->d_gen ? s->d_gen + old : nullptr;
-    fp.ge = s->d_gen ? s->d_gen + 2 + old : nullptr;
-    return SBP_OK;
-}
-
-// Upload the general-path parameters the fused sweep reads in x/y mode.
-int upload_gen(sbp_sim *s)
-{
-    if (!s->fused_xy || (!s->gen_dirty && s->d_gen)) return SBP_OK;
-    if (!s->d_gen) SBP_CUDA(cudaMalloc(&s->d_gen, 4 * sizeof(sbp::Params<float>)));
-    sbp::Params<float> h[4];
-    int rc;
-    for (int c = 0; c < 2; c++) {
-        if ((rc = make_params<float>(s, h[c], c, c))) return rc;
-        if ((rc = make_params<float>(s, h[2 + c], c, c ^ 1))) return rc;
-    }
-    SBP_CUDA(cudaMemcpyAsync(s->d_gen, h, sizeof(h), cudaMemcpyHostToDevice, s->stream));
-    SBP_CUDA(cudaStreamSynchronize(s->stream));
-    s->gen_dirty = false;
     return SBP_OK;
 }
 
@@ -514,9 +457,7 @@ int launch_fused_interior_only(sbp_sim *s)
 {
     const int old = s->cur;
     sbp::FusedParams fp;
-    int rc = upload_gen(s);
-    if (rc) return rc;
-    rc = make_fused_params(s, old, fp);
+    int rc = make_fused_params(s, old, fp);
     if (rc) return rc;
     rc = set_fused_smem_attr();
     if (rc) return rc;
@@ -904,8 +845,6 @@ int batch_rebuild(sbp_batch *b)
         for (int c = 0; c < 2; c++) {
             G.maps[c] = s->maps[c];
             if ((rc = make_fused_params(s, c, G.fp[c]))) return rc;
-            G.fp[c].gh = &b->d_grids[g].ph[c];           // device addresses of this grid's entries
-            G.fp[c].ge = &b->d_grids[g].pe[c];
             if ((rc = make_params<float>(s, G.ph[c], c, c))) return rc;
             if ((rc = make_params<float>(s, G.pe[c], c, c ^ 1))) return rc;
             for (int f = 0; f < 3; f++) {
@@ -993,13 +932,6 @@ int sbp_connect(sbp_sim *a, int fa, sbp_sim *b, int fb)
     if (a->dt != b->dt) return SBP_ENOTCONFORMING;
     a->face[fa] = SBP_INTERFACE; a->nbr[fa] = b; a->nbr_face[fa] = fb;
     b->face[fb] = SBP_INTERFACE; b->nbr[fb] = a; b->nbr_face[fb] = fa;
-    for (sbp_sim *s : {a, b}) {
-        s->gen_dirty = true;
-        if (s->fused_ok) {
-            int rc = configure_fused(s);
-            if (rc) return rc;
-        }
-    }
     return SBP_OK;
 }
 
@@ -1049,7 +981,6 @@ int sbp_add_source(sbp_sim *s, int comp, int i, int j, int k, int waveform, doub
     q.comp = comp; q.i = i; q.j = j; q.k = k; q.wf = waveform;
     q.amp = amp; q.tw = tw; q.t0 = t0; q.f = f;
     s->src.push_back(q);
-    s->gen_dirty = true;
     return (int)s->src.size() - 1;
 }
 
@@ -1065,7 +996,6 @@ int sbp_add_probe(sbp_sim *s, int comp, int i, int j, int k, int *probe_id)
     sbp::Prb q;
     q.comp = comp; q.i = i; q.j = j; q.k = k;
     s->prb.push_back(q);
-    s->gen_dirty = true;
     if (probe_id) *probe_id = (int)s->prb.size() - 1;
     return SBP_OK;
 }
@@ -1084,7 +1014,6 @@ int sbp_reserve_probes(sbp_sim *s, int64_t nsteps)
         s->probe_cap = nsteps;
     }
     s->probe_base = s->step;
-    s->gen_dirty = true;
     return SBP_OK;
 }
 
@@ -1229,7 +1158,6 @@ int sbp_destroy(sbp_sim *s)
     if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->probe_buf) cudaFree(s->probe_buf);
     if (s->eseries) cudaFree(s->eseries);
-    if (s->d_gen) cudaFree(s->d_gen);
     if (s->own_ws && s->workspace) cudaFree(s->workspace);
     delete s;
     return SBP_OK;
