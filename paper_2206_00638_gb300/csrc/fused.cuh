@@ -328,131 +328,222 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interio
 
 // ---------------------------------------------------------------------------
 // Band kernels: every node outside the interior box [lo, hi_a] of its phase.
-// The band is split into disjoint slabs: full z-planes below lo / above hi,
-// then full y-rows of the remaining planes, then the x-ends of what is left.
+// The band is split into disjoint slabs: the x-ends (i < lo or i > hi_x, every
+// j and k), then the y-ends of the rest (every k), then the z-ends of the
+// rest.  Work goes out by warps: a warp of the z or y slab takes up to 32
+// consecutive nodes of one x-row (coalesced), a warp of the x slab 4 x-end
+// nodes of 8 consecutive rows of one plane.  Every index is decoded once per
+// warp, and each warp knows which axes can put its nodes on a closure row or
+// a face (G); along the others its nodes are interior and take the two-point
+// row, the same expression the general row evaluates there.
 // ---------------------------------------------------------------------------
 struct Band {
-    int lo;
-    int hi[3];               // interior box upper bound per axis (inclusive)
-    long long nz_slab, ny_slab, nx_slab;   // node counts of the three slabs
+    int lo;                   // interior box lower bound (every axis)
+    int hi[3];                // interior box upper bound per axis (inclusive)
+    unsigned segs;            // 32-node x segments from x = 0 up to hi_x
+    unsigned zplanes;         // planes of the z slab
+    unsigned yrows;           // rows per plane of the y slab
+    unsigned jin;             // interior rows (z slab rows per plane)
+    unsigned xgroups;         // 8-row groups per plane of the x slab
+    unsigned wz, wy, wx;      // warps of the three slabs
+    unsigned ctas;            // CTAs of 256 threads over all warps
 };
 
-__device__ __forceinline__ void band_node(const Band &b, const int n[3], long long tl, int &i, int &j, int &k)
+// Node of `lane` in band warp w, the warp's index box [il,ih] x [jl,jh] x {k}
+// and its closure axes G (bit a).  False when the lane has no node.
+__device__ __forceinline__ bool band_lane(const Band &b, const int n[3], unsigned w, int lane, int &i, int &j, int &k,
+                                          int &il, int &ih, int &jl, int &jh, int &G)
 {
-    // 32-bit index arithmetic: every slab of a grid this library accepts has
-    // fewer than 2^32 nodes (the host checks), and 64-bit division is slow.
-    const unsigned ex = n[0] + 2, ey = n[1] + 2;
     const int lo = b.lo;
-    unsigned t = (unsigned)tl;
-    if (tl < b.nz_slab) {
-        const unsigned plane = t / (ex * ey);
-        const unsigned r = t - plane * (ex * ey);
-        k = (int)plane < lo ? (int)plane : b.hi[2] + 1 + ((int)plane - lo);
-        j = (int)(r / ex);
-        i = (int)(r - (unsigned)j * ex);
-        return;
+    if (w < b.wz + b.wy) {
+        const bool zs = w < b.wz;
+        if (!zs) w -= b.wz;
+        const unsigned r = w / b.segs;
+        const unsigned seg = w - r * b.segs;
+        if (zs) {
+            const unsigned pl = r / b.jin;
+            j = lo + (int)(r - pl * b.jin);
+            k = (int)pl < lo ? (int)pl : b.hi[2] + 1 + ((int)pl - lo);
+            G = 4;
+        } else {
+            const unsigned kk = r / b.yrows;
+            const int jr = (int)(r - kk * b.yrows);
+            k = (int)kk;
+            j = jr < lo ? jr : b.hi[1] + 1 + (jr - lo);
+            G = (k < lo || k > b.hi[2]) ? 6 : 2;
+        }
+        jl = jh = j;
+        il = (int)seg * 32;
+        ih = il + 31;
+        i = il + lane;
+        return i >= lo && i <= b.hi[0];
     }
-    t = (unsigned)(tl - b.nz_slab);
-    const unsigned nyr = lo + (n[1] + 1 - b.hi[1]);   // rows below lo and above hi
-    if (tl - b.nz_slab < b.ny_slab) {
-        const unsigned per_k = nyr * ex;
-        const unsigned kk = t / per_k;
-        const unsigned r = t - kk * per_k;
-        const unsigned yr = r / ex;
-        k = lo + (int)kk;
-        j = (int)yr < lo ? (int)yr : b.hi[1] + 1 + ((int)yr - lo);
-        i = (int)(r - yr * ex);
-        return;
-    }
-    t = (unsigned)(tl - b.nz_slab - b.ny_slab);
-    const unsigned nxr = lo + (n[0] + 1 - b.hi[0]);
-    const unsigned nyin = b.hi[1] - lo + 1;
-    const unsigned per_k = nyin * nxr;
-    const unsigned kk = t / per_k;
-    const unsigned r = t - kk * per_k;
-    const unsigned yy = r / nxr;
-    const unsigned xr = r - yy * nxr;
-    k = lo + (int)kk;
-    j = lo + (int)yy;
-    i = (int)xr < lo ? (int)xr : b.hi[0] + 1 + ((int)xr - lo);
+    w -= b.wz + b.wy;
+    const unsigned side = w & 1u, r = w >> 1;
+    const unsigned kk = r / b.xgroups;
+    const int g = (int)(r - kk * b.xgroups);
+    k = (int)kk;
+    jl = 8 * g;
+    jh = min(jl + 7, n[1] + 1);
+    j = jl + (lane >> 2);
+    const int c = lane & 3;
+    il = side ? b.hi[0] + 1 : 0;
+    ih = il + 3;
+    i = il + c;
+    G = 1 | ((jl < lo || jh > b.hi[1]) ? 2 : 0) | ((k < lo || k > b.hi[2]) ? 4 : 0);
+    return j <= jh && (side ? i <= n[0] + 1 : c < lo);
 }
 
-// H^{n+1/2} at band node t: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
+// Probes of components [c0, c0+2] inside the warp's box (one bit per probe).
+__device__ __forceinline__ unsigned long long warp_probe_mask(const Prb *prb, int nprb, int c0, int k, int il, int ih,
+                                                              int jl, int jh, int lane)
+{
+    unsigned long long m = 0ull;
+    for (int q0 = 0; q0 < nprb; q0 += 32) {
+        const int q = q0 + lane;
+        bool hit = false;
+        if (q < nprb) {
+            const Prb P = prb[q];
+            hit = P.comp >= c0 && P.comp <= c0 + 2 && P.k == k && P.j >= jl && P.j <= jh && P.i >= il && P.i <= ih;
+        }
+        m |= (unsigned long long)__ballot_sync(0xffffffffu, hit) << q0;
+    }
+    return m;
+}
+
+template <typename T>
+__device__ __forceinline__ void band_probes(const Params<T> &p, unsigned long long m, int c0, int i, int j,
+                                            long long pslot, const T v[3], const bool have[3])
+{
+    while (m) {
+        const int q = __ffsll((long long)m) - 1;
+        m &= m - 1;
+        const Prb &P = p.prb[q];
+        const int c = P.comp - c0;
+        const bool hv = c == 0 ? have[0] : c == 1 ? have[1] : have[2];
+        if (P.i == i && P.j == j && hv && pslot < p.probe_cap)
+            p.probe_buf[(long long)q * p.probe_cap + pslot] = c == 0 ? v[0] : c == 1 ? v[1] : v[2];
+    }
+}
+
+// H^{n+1/2} at one band node, closure axes G: every load first (in bounds for
+// all three components: the node and its row entries lie in the padded
+// layout), then the updates.
+template <typename T, bool MUVAR, int G>
+__device__ __forceinline__ void band_h_at(const Params<T> &p, const int idx[3], long long o, const bool have[3],
+                                          T *const outs[3], T hn[3])
+{
+    Tri<T> vx[2], vy[2], vz[2];
+    h_gather<T, 3, G>(p, idx, o, vx);
+    h_gather<T, 4, G>(p, idx, o, vy);
+    h_gather<T, 5, G>(p, idx, o, vz);
+    const T hx = p.F[3][o], hy = p.F[4][o], hz = p.F[5][o];
+    if (have[0]) outs[0][o] = hn[0] = h_apply<T, 3, MUVAR, G>(p, idx, o, hx, vx);
+    if (have[1]) outs[1][o] = hn[1] = h_apply<T, 4, MUVAR, G>(p, idx, o, hy, vy);
+    if (have[2]) outs[2][o] = hn[2] = h_apply<T, 5, MUVAR, G>(p, idx, o, hz, vz);
+}
+
+// H^{n+1/2} at the nodes of band warp w: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
 template <typename T, bool MUVAR>
-__device__ __forceinline__ void band_h_node(const Params<T> &p, const Band &b, long long t, long long pslot,
+__device__ __forceinline__ void band_h_warp(const Params<T> &p, const Band &b, unsigned w, int lane, long long pslot,
                                             T *const outs[3])
 {
-    int i, j, k;
-    band_node(b, p.n, t, i, j, k);
+    int i, j, k, il, ih, jl, jh, G;
+    const bool valid = band_lane(b, p.n, w, lane, i, j, k, il, ih, jl, jh, G);
+    const unsigned long long pm = p.nprb ? warp_probe_mask(p.prb, p.nprb, 3, k, il, ih, jl, jh, lane) : 0ull;
+    if (!valid) return;
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int idx[3] = {i, j, k};
     const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
     T hn[3];
-    bool have[3] = {i <= nx && j <= ny + 1 && k <= nz + 1, i <= nx + 1 && j <= ny && k <= nz + 1,
-                    i <= nx + 1 && j <= ny + 1 && k <= nz};
-    if (have[0]) hn[0] = h_node<T, 3, MUVAR>(p, idx, o, p.F[3][o]);
-    if (have[1]) hn[1] = h_node<T, 4, MUVAR>(p, idx, o, p.F[4][o]);
-    if (have[2]) hn[2] = h_node<T, 5, MUVAR>(p, idx, o, p.F[5][o]);
-    for (int c = 0; c < 3; ++c) {
-        if (!have[c]) continue;
-        outs[c][o] = hn[c];
-        for (int q = 0; q < p.nprb; ++q) {
-            const Prb &P = p.prb[q];
-            if (P.comp == 3 + c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
-                p.probe_buf[(long long)q * p.probe_cap + pslot] = hn[c];
-        }
+    const bool have[3] = {i <= nx && j <= ny + 1 && k <= nz + 1, i <= nx + 1 && j <= ny && k <= nz + 1,
+                          i <= nx + 1 && j <= ny + 1 && k <= nz};
+    switch (G) {   // uniform per warp
+    case 4: band_h_at<T, MUVAR, 4>(p, idx, o, have, outs, hn); break;
+    case 2: band_h_at<T, MUVAR, 2>(p, idx, o, have, outs, hn); break;
+    case 6: band_h_at<T, MUVAR, 6>(p, idx, o, have, outs, hn); break;
+    case 1: band_h_at<T, MUVAR, 1>(p, idx, o, have, outs, hn); break;
+    default: band_h_at<T, MUVAR, 7>(p, idx, o, have, outs, hn); break;
     }
+    if (pm) band_probes(p, pm, 3, i, j, pslot, hn, have);
 }
 
 template <typename T, bool MUVAR>
 __global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T *hx_out, T *hy_out, T *hz_out)
 {
-    const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= total) return;
+    const unsigned w = blockIdx.x * 8u + (threadIdx.x >> 5);
+    if (w >= b.wz + b.wy + b.wx) return;
     T *const outs[3] = {hx_out, hy_out, hz_out};
-    band_h_node<T, MUVAR>(p, b, t, p.probe_slot, outs);
+    band_h_warp<T, MUVAR>(p, b, w, threadIdx.x & 31, p.probe_slot, outs);
 }
 
-// E^{n+1} at band node t: p.F = {E^n (old), H^{n+1/2} (new)}, outs = new E.
+// E^{n+1} at one band node, closure axes G (see band_h_at).
+template <typename T, bool MUVAR, int G>
+__device__ __forceinline__ void band_e_at(const Params<T> &p, const int idx[3], long long o, const bool have[3],
+                                          unsigned sm, double t_half, T *const outs[3], T en[3])
+{
+    Tri<T> vx[2], vy[2], vz[2];
+    e_gather<T, 0, false, G>(p, idx, o, vx);
+    e_gather<T, 1, false, G>(p, idx, o, vy);
+    e_gather<T, 2, false, G>(p, idx, o, vz);
+    const T ex = p.F[0][o], ey = p.F[1][o], ez = p.F[2][o];
+    const T sx = cell_sum<0, T>(p.eps, o, p.sy, p.sz);
+    const T sy = cell_sum<1, T>(p.eps, o, p.sy, p.sz);
+    const T sz = cell_sum<2, T>(p.eps, o, p.sy, p.sz);
+    if (have[0]) outs[0][o] = en[0] = e_apply<T, 0, MUVAR, false, G>(p, idx, o, ex, sx, vx, sm, t_half);
+    if (have[1]) outs[1][o] = en[1] = e_apply<T, 1, MUVAR, false, G>(p, idx, o, ey, sy, vy, sm, t_half);
+    if (have[2]) outs[2][o] = en[2] = e_apply<T, 2, MUVAR, false, G>(p, idx, o, ez, sz, vz, sm, t_half);
+}
+
+// E^{n+1} at the nodes of band warp w: p.F = {E^n (old), H^{n+1/2} (new)}, outs = new E.
 template <typename T, bool MUVAR>
-__device__ __forceinline__ void band_e_node(const Params<T> &p, const Band &b, long long t, long long step,
+__device__ __forceinline__ void band_e_warp(const Params<T> &p, const Band &b, unsigned w, int lane, long long step,
                                             long long pslot, T *const outs[3])
 {
-    int i, j, k;
-    band_node(b, p.n, t, i, j, k);
+    int i, j, k, il, ih, jl, jh, G;
+    const bool valid = band_lane(b, p.n, w, lane, i, j, k, il, ih, jl, jh, G);
+    const unsigned long long pm = p.nprb ? warp_probe_mask(p.prb, p.nprb, 0, k, il, ih, jl, jh, lane) : 0ull;
+    // sources that can reach the warp's box (point, line or sheet), then this node's
+    unsigned wm = 0u;
+    if (p.nsrc) {
+        bool hit = false;
+        if (lane < p.nsrc) {
+            const Src &S = p.src[lane];
+            hit = (S.i < 0 || (S.i >= il && S.i <= ih)) && (S.j < 0 || (S.j >= jl && S.j <= jh)) &&
+                  (S.k < 0 || S.k == k);
+        }
+        wm = __ballot_sync(0xffffffffu, hit);
+    }
+    if (!valid) return;
+    unsigned sm = 0u;
+    for (unsigned m = wm; m; m &= m - 1) {
+        const int q = __ffs(m) - 1;
+        if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) sm |= 1u << q;
+    }
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int idx[3] = {i, j, k};
     const long long o = (long long)k * p.sz + (long long)j * p.sy + i;
-    unsigned sm = 0u;
-    for (int q = 0; q < p.nsrc; ++q)
-        if ((p.src[q].i < 0 || p.src[q].i == i) && (p.src[q].j < 0 || p.src[q].j == j)) sm |= 1u << q;
     const double t_half = ((double)step + 0.5) * p.dt;
     T en[3];
-    bool have[3] = {i <= nx + 1 && j <= ny && k <= nz, i <= nx && j <= ny + 1 && k <= nz,
-                    i <= nx && j <= ny && k <= nz + 1};
-    if (have[0]) en[0] = e_node<T, 0, MUVAR>(p, idx, o, p.F[0][o], sm, t_half);
-    if (have[1]) en[1] = e_node<T, 1, MUVAR>(p, idx, o, p.F[1][o], sm, t_half);
-    if (have[2]) en[2] = e_node<T, 2, MUVAR>(p, idx, o, p.F[2][o], sm, t_half);
-    for (int c = 0; c < 3; ++c) {
-        if (!have[c]) continue;
-        outs[c][o] = en[c];
-        for (int q = 0; q < p.nprb; ++q) {
-            const Prb &P = p.prb[q];
-            if (P.comp == c && P.i == i && P.j == j && P.k == k && pslot < p.probe_cap)
-                p.probe_buf[(long long)q * p.probe_cap + pslot] = en[c];
-        }
+    const bool have[3] = {i <= nx + 1 && j <= ny && k <= nz, i <= nx && j <= ny + 1 && k <= nz,
+                          i <= nx && j <= ny && k <= nz + 1};
+    switch (G) {   // uniform per warp
+    case 4: band_e_at<T, MUVAR, 4>(p, idx, o, have, sm, t_half, outs, en); break;
+    case 2: band_e_at<T, MUVAR, 2>(p, idx, o, have, sm, t_half, outs, en); break;
+    case 6: band_e_at<T, MUVAR, 6>(p, idx, o, have, sm, t_half, outs, en); break;
+    case 1: band_e_at<T, MUVAR, 1>(p, idx, o, have, sm, t_half, outs, en); break;
+    default: band_e_at<T, MUVAR, 7>(p, idx, o, have, sm, t_half, outs, en); break;
     }
+    if (pm) band_probes(p, pm, 0, i, j, pslot, en, have);
 }
 
 template <typename T, bool MUVAR>
 __global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T *ex_out, T *ey_out, T *ez_out)
 {
-    const long long total = b.nz_slab + b.ny_slab + b.nx_slab;
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= total) return;
+    const unsigned w = blockIdx.x * 8u + (threadIdx.x >> 5);
+    if (w >= b.wz + b.wy + b.wx) return;
     T *const outs[3] = {ex_out, ey_out, ez_out};
-    band_e_node<T, MUVAR>(p, b, t, p.step, p.probe_slot, outs);
+    band_e_warp<T, MUVAR>(p, b, w, threadIdx.x & 31, p.step, p.probe_slot, outs);
 }
 
 // ---------------------------------------------------------------------------
@@ -520,9 +611,9 @@ __global__ void __launch_bounds__(256) band_h_batched(const BatchGrid *G, const 
     long long step;
     int par;
     if (!batch_state(B, offset, step, par)) return;
-    const long long t = (long long)(blockIdx.x - pre[g]) * blockDim.x + threadIdx.x;
-    if (t >= B.bh.nz_slab + B.bh.ny_slab + B.bh.nx_slab) return;
-    band_h_node<float, false>(B.ph[par], B.bh, t, step - B.probe_base, B.hout[par]);
+    const unsigned w = (unsigned)(blockIdx.x - pre[g]) * 8u + (threadIdx.x >> 5);
+    if (w >= B.bh.wz + B.bh.wy + B.bh.wx) return;
+    band_h_warp<float, false>(B.ph[par], B.bh, w, threadIdx.x & 31, step - B.probe_base, B.hout[par]);
 }
 
 __global__ void __launch_bounds__(256) band_e_batched(const BatchGrid *G, const int *pre, int n, int offset)
@@ -532,9 +623,9 @@ __global__ void __launch_bounds__(256) band_e_batched(const BatchGrid *G, const 
     long long step;
     int par;
     if (!batch_state(B, offset, step, par)) return;
-    const long long t = (long long)(blockIdx.x - pre[g]) * blockDim.x + threadIdx.x;
-    if (t >= B.be.nz_slab + B.be.ny_slab + B.be.nx_slab) return;
-    band_e_node<float, false>(B.pe[par], B.be, t, step, step - B.probe_base, B.eout[par]);
+    const unsigned w = (unsigned)(blockIdx.x - pre[g]) * 8u + (threadIdx.x >> 5);
+    if (w >= B.be.wz + B.be.wy + B.be.wx) return;
+    band_e_warp<float, false>(B.pe[par], B.be, w, threadIdx.x & 31, step, step - B.probe_base, B.eout[par]);
 }
 
 __global__ void batch_advance(const BatchGrid *G, int n, long long k)

@@ -133,18 +133,13 @@ __device__ __forceinline__ double scaled_increment(const Acc<double> &a, double 
 __device__ __forceinline__ float plain_increment(const Acc<float> &a) { return a.hi + a.lo; }
 __device__ __forceinline__ double plain_increment(const Acc<double> &a) { return a.hi; }
 
-// Rows of the Appendix operators at unit spacing.  u points at node 0 of the
-// line, s is the stride along the axis, r the output row, n the cell count.
-// D- : x+ (n+1 values) -> x- (n+2 rows).
-template <typename T>
-__device__ __forceinline__ T dminus_row(const T *__restrict__ u, long long s, int r, int n)
-{
-    if (r == 0) return u[s] - u[0];
-    if (r == 2) return (T(4) * u[2 * s] - T(3) * u[s] - u[0]) * T(0.2);
-    if (r == n - 1) return (u[n * s] + T(3) * u[(n - 1) * s] - T(4) * u[(n - 2) * s]) * T(0.2);
-    if (r == n + 1) return u[n * s] - u[(n - 1) * s];
-    return u[r * s] - u[(r - 1) * s];          // rows 1, 3..n-2, n
-}
+// Rows of the Appendix operators at unit spacing.  Every row reads at most
+// three consecutive entries of its line; they are gathered first (no branch
+// before the loads, so all of a node's loads are in flight together) and the
+// row formula is then applied to them.  The line holds entries 0..n+1 of the
+// padded layout, so the gathered triple is always in bounds.
+template <typename T> struct Tri { T a, b, c; };
+
 // Field load; CG = true reads through L2 only (ld.global.cg), for values this
 // kernel itself wrote earlier (coherent across the threads of a CTA after a
 // barrier, never served stale from L1 or the read-only path).
@@ -155,16 +150,41 @@ __device__ __forceinline__ T ldf(const T *p)
     else return *p;
 }
 
-// D+ : x- (n+2 values) -> x+ (n+1 rows).
-template <typename T, bool CG = false>
-__device__ __forceinline__ T dplus_row(const T *v, long long s, int r, int n)
+// entries s0, s0+1, s0+2 of the line starting at `line` with stride s
+template <bool CG, typename T>
+__device__ __forceinline__ Tri<T> tri_load(const T *line, long long s, int s0)
 {
-    if (r == 0) return T(0.5) * (ldf<CG>(v + s) + ldf<CG>(v + 2 * s)) - ldf<CG>(v);
-    if (r == 1) return T(0.75) * ldf<CG>(v + 2 * s) - T(0.5) * ldf<CG>(v) - T(0.25) * ldf<CG>(v + s);
-    if (r == n - 1)
-        return T(0.25) * ldf<CG>(v + n * s) + T(0.5) * ldf<CG>(v + (n + 1) * s) - T(0.75) * ldf<CG>(v + (n - 1) * s);
-    if (r == n) return ldf<CG>(v + (n + 1) * s) - T(0.5) * (ldf<CG>(v + (n - 1) * s) + ldf<CG>(v + n * s));
-    return ldf<CG>(v + (r + 1) * s) - ldf<CG>(v + r * s);          // rows 2..n-2
+    const T *q = line + (long long)s0 * s;
+    return {ldf<CG>(q), ldf<CG>(q + s), ldf<CG>(q + 2 * s)};
+}
+
+// D- : x+ (n+1 values) -> x- (n+2 rows).  First entry read by row r.
+__device__ __forceinline__ int dminus_start(int r, int n)
+{
+    return (r == 0 || r == 2) ? 0 : (r == n - 1 || r == n + 1) ? n - 2 : r - 1;
+}
+// Row r of D- from the entries gathered at dminus_start(r, n).
+template <typename T>
+__device__ __forceinline__ T dminus_eval(const Tri<T> &u, int r, int n)
+{
+    if (r == 0) return u.b - u.a;                                          // u1 - u0
+    if (r == 2) return (T(4) * u.c - T(3) * u.b - u.a) * T(0.2);           // (4u2 - 3u1 - u0) / 5
+    if (r == n - 1) return (u.c + T(3) * u.b - T(4) * u.a) * T(0.2);       // (u_n + 3u_{n-1} - 4u_{n-2}) / 5
+    if (r == n + 1) return u.c - u.b;                                      // u_n - u_{n-1}
+    return u.b - u.a;                                                      // rows 1, 3..n-2, n: u_r - u_{r-1}
+}
+
+// D+ : x- (n+2 values) -> x+ (n+1 rows).  First entry read by row r.
+__device__ __forceinline__ int dplus_start(int r, int n) { return r <= 1 ? 0 : r >= n - 1 ? n - 1 : r; }
+// Row r of D+ from the entries gathered at dplus_start(r, n).
+template <typename T>
+__device__ __forceinline__ T dplus_eval(const Tri<T> &v, int r, int n)
+{
+    if (r == 0) return T(0.5) * (v.b + v.c) - v.a;                         // (v1 + v2)/2 - v0
+    if (r == 1) return T(0.75) * v.c - T(0.5) * v.a - T(0.25) * v.b;       // 3v2/4 - v0/2 - v1/4
+    if (r == n - 1) return T(0.25) * v.b + T(0.5) * v.c - T(0.75) * v.a;   // v_n/4 + v_{n+1}/2 - 3v_{n-1}/4
+    if (r == n) return v.c - T(0.5) * (v.a + v.b);                         // v_{n+1} - (v_{n-1} + v_n)/2
+    return v.b - v.a;                                                      // rows 2..n-2: v_{r+1} - v_r
 }
 
 // 1D norm weight (unit spacing) of node r: P+ = diag(1/2,1,...,1,1/2),
@@ -274,26 +294,46 @@ __device__ __forceinline__ void block_sum_to(double v, double *dst)
 // ---------------------------------------------------------------------------
 // H half-step: general path for one component at one node
 // ---------------------------------------------------------------------------
-template <typename T, int C, bool MUVAR>
-__device__ __forceinline__ T h_node(const Params<T> &p, const int idx[3], long long o, T hold)
+// Entries of E read by the two curl terms of H component C at node idx.
+// G: bit a set when the node may lie on a closure row or face along axis a;
+// along the other axes the node is interior and the row is u_r - u_{r-1}.
+template <typename T, int C, int G = 7>
+__device__ __forceinline__ void h_gather(const Params<T> &p, const int idx[3], long long o, Tri<T> v[2])
+{
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int u = curl_comp(C, t), a = curl_axis(C, t);
+        const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
+        if ((G >> a) & 1) {
+            v[t] = tri_load<false>(p.F[u] + (o - idx[a] * st), st, dminus_start(idx[a], p.n[a]));
+        } else {
+            v[t].a = p.F[u][o - st];
+            v[t].b = p.F[u][o];
+            v[t].c = v[t].b;
+        }
+    }
+}
+
+// H^{n+1/2} of component C at node idx from H^{n-1/2} (hold) and the gathered E.
+template <typename T, int C, bool MUVAR, int G = 7>
+__device__ __forceinline__ T h_apply(const Params<T> &p, const int idx[3], long long o, T hold, const Tri<T> v[2])
 {
     Acc<T> acc;
     T gam = T(0);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int u = curl_comp(C, t), a = curl_axis(C, t), sg = curl_sign(t);
-        const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
-        const T *line = p.F[u] + (o - idx[a] * st);
-        const T d = dminus_row(line, st, idx[a], p.n[a]);
+        const bool gen = (G >> a) & 1;
+        const T d = gen ? dminus_eval(v[t], idx[a], p.n[a]) : v[t].b - v[t].a;
         acc.add(p.B[a], d, T(sg));
         // H on the minus grid along a: face nodes at 0 and n+1 carry the SAT
-        if (idx[a] == 0 || idx[a] == p.n[a] + 1) {
+        if (gen && (idx[a] == 0 || idx[a] == p.n[a] + 1)) {
             const int side = idx[a] == 0 ? -1 : 1;
             const int f = 2 * a + (side > 0);
             const int type = p.face[f];
             if (type != kPMC) {
                 const T phi = T(-sg * side);
-                const T pv = line[(side < 0 ? 0 : p.n[a]) * st];
+                const T pv = side < 0 ? v[t].a : v[t].c;      // E on the face: entry 0 or n
                 if (type == kPEC) {
                     acc.add(p.B[a], pv, T(2) * phi);
                 } else if (type == kABS) {
@@ -326,29 +366,56 @@ __device__ __forceinline__ T h_node(const Params<T> &p, const int idx[3], long l
     return hold + inc;
 }
 
-// E half-step: general path for one component at one node.
-template <typename T, int C, bool MUVAR, bool CG = false>
-__device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long long o, T eold,
-                                    unsigned smask, double t_half)
+// H half-step, general path, one component at one node (Eqs. (10)-(15)).
+template <typename T, int C, bool MUVAR>
+__device__ __forceinline__ T h_node(const Params<T> &p, const int idx[3], long long o, T hold)
+{
+    Tri<T> v[2];
+    h_gather<T, C>(p, idx, o, v);
+    return h_apply<T, C, MUVAR>(p, idx, o, hold, v);
+}
+
+// Entries of H read by the two curl terms of E component C at node idx.
+// G as for h_gather; interior rows of D+ are v_{r+1} - v_r.
+template <typename T, int C, bool CG = false, int G = 7>
+__device__ __forceinline__ void e_gather(const Params<T> &p, const int idx[3], long long o, Tri<T> v[2])
+{
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const int u = curl_comp(C, t), a = curl_axis(C, t);
+        const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
+        if ((G >> a) & 1) {
+            v[t] = tri_load<CG>(p.F[u] + (o - idx[a] * st), st, dplus_start(idx[a], p.n[a]));
+        } else {
+            v[t].a = ldf<CG>(p.F[u] + o);
+            v[t].b = ldf<CG>(p.F[u] + o + st);
+            v[t].c = v[t].b;
+        }
+    }
+}
+
+// E^{n+1} of component C at node idx from E^n (eold), se = sum4 eps_r of the
+// node and the gathered H.
+template <typename T, int C, bool MUVAR, bool CG = false, int G = 7>
+__device__ __forceinline__ T e_apply(const Params<T> &p, const int idx[3], long long o, T eold, T se, const Tri<T> v[2],
+                                     unsigned smask, double t_half)
 {
     Acc<T> acc;
     T gam = T(0);
-    const T se = cell_sum<C, T>(p.eps, o, p.sy, p.sz);     // 4 * eps_r(node)
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const int u = curl_comp(C, t), a = curl_axis(C, t), sg = curl_sign(t);
-        const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
-        const T *line = p.F[u] + (o - idx[a] * st);
-        const T d = dplus_row<T, CG>(line, st, idx[a], p.n[a]);
+        const bool gen = (G >> a) & 1;
+        const T d = gen ? dplus_eval(v[t], idx[a], p.n[a]) : v[t].b - v[t].a;
         acc.add(p.A[a], d, T(sg));
         // E on the plus grid along a: face nodes at 0 and n carry the SAT
-        if (idx[a] == 0 || idx[a] == p.n[a]) {
+        if (gen && (idx[a] == 0 || idx[a] == p.n[a])) {
             const int side = idx[a] == 0 ? -1 : 1;
             const int f = 2 * a + (side > 0);
             const int type = p.face[f];
             if (type != kPEC) {
                 const T phi = T(-sg * side);
-                const T pv = ldf<CG>(line + (side < 0 ? 0 : p.n[a] + 1) * st);
+                const T pv = side < 0 ? v[t].a : v[t].c;      // H on the face: entry 0 or n+1
                 if (type == kPMC) {
                     acc.add(p.A[a], pv, T(2) * phi);
                 } else if (type == kABS) {
@@ -384,6 +451,17 @@ __device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long l
     const T inc = scaled_increment(acc, se);
     if (gam != T(0)) return ((T(1) - gam) * eold + inc) / (T(1) + gam);
     return eold + inc;
+}
+
+// E half-step, general path, one component at one node (Eqs. (7)-(9), (19)-(21)).
+template <typename T, int C, bool MUVAR, bool CG = false>
+__device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long long o, T eold,
+                                    unsigned smask, double t_half)
+{
+    const T se = cell_sum<C, T>(p.eps, o, p.sy, p.sz);     // 4 * eps_r(node)
+    Tri<T> v[2];
+    e_gather<T, C, CG>(p, idx, o, v);
+    return e_apply<T, C, MUVAR, CG>(p, idx, o, eold, se, v, smask, t_half);
 }
 
 // ---------------------------------------------------------------------------

@@ -291,15 +291,36 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
         SBP_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
         SBP_CUDA(cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming));
         SBP_CUDA(cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming));
+        // The one-pass step covers H on [3, n-2] and E on [3, n-3] per axis.
+        // The H band also takes the first interior layer (H on [4, n-3] is
+        // left to the one-pass step alone): an E band node reads H at most
+        // one node inward along each axis (D+ rows 0..2 read H 0..3, row n-2
+        // reads H n-2, n-1), so band E depends on band H only and both run
+        // beside the one-pass step.  Both kernels write that layer with the
+        // same formula and the same rounding, hence the same bits.
         for (int phase = 0; phase < 2; phase++) {
             sbp::Band &b = phase == 0 ? s->band_hb : s->band_eb;
-            b.lo = 3;
-            for (int a = 0; a < 3; a++) b.hi[a] = s->n[a] - (phase == 0 ? 2 : 3);
-            const long long ex = s->n[0] + 2, ey = s->n[1] + 2;
-            b.nz_slab = (long long)(b.lo + (s->n[2] + 1 - b.hi[2])) * ex * ey;
-            b.ny_slab = (long long)(b.hi[2] - b.lo + 1) * (b.lo + (s->n[1] + 1 - b.hi[1])) * ex;
-            b.nx_slab = (long long)(b.hi[2] - b.lo + 1) * (b.hi[1] - b.lo + 1) * (b.lo + (s->n[0] + 1 - b.hi[0]));
-            if (b.nz_slab >= (1ll << 32) || b.ny_slab >= (1ll << 32) || b.nx_slab >= (1ll << 32)) return SBP_EINVAL;
+            b.lo = phase == 0 ? 4 : 3;
+            for (int a = 0; a < 3; a++) b.hi[a] = s->n[a] - 3;
+            // warps: 32-node x-row segments (x in [lo, hi_x]) for the z and
+            // y slabs, 4 x-end nodes x 8 rows for the x slab (both x-ends at
+            // most 4 wide; segments start at x = 0, so lo < 32)
+            if (b.lo > 4 || s->n[0] + 1 - b.hi[0] > 4) return SBP_EINVAL;
+            const long long segs = b.hi[0] / 32 + 1, ey = s->n[1] + 2, ez = s->n[2] + 2;
+            const long long zplanes = b.lo + (s->n[2] + 1 - b.hi[2]);
+            const long long yrows = b.lo + (s->n[1] + 1 - b.hi[1]);
+            const long long jin = b.hi[1] - b.lo + 1, xgroups = (ey + 7) / 8;
+            const long long wz = zplanes * jin * segs, wy = ez * yrows * segs, wx = ez * xgroups * 2;
+            if (wz + wy + wx >= (1ll << 32) - 8) return SBP_EINVAL;
+            b.segs = (unsigned)segs;
+            b.zplanes = (unsigned)zplanes;
+            b.yrows = (unsigned)yrows;
+            b.jin = (unsigned)jin;
+            b.xgroups = (unsigned)xgroups;
+            b.wz = (unsigned)wz;
+            b.wy = (unsigned)wy;
+            b.wx = (unsigned)wx;
+            b.ctas = (unsigned)((wz + wy + wx + 7) / 8);
         }
     }
     return SBP_OK;
@@ -469,41 +490,53 @@ int launch_fused_interior_only(sbp_sim *s)
     return SBP_OK;
 }
 
-// Fused path, phase 1: band H (old -> new) on the side stream, concurrently
-// with the one-pass interior step on the main stream; joined before phase 2.
-int launch_fused_phase1(sbp_sim *s)
-{
-    const int old = s->cur, nw = s->cur ^ 1;
-    sbp::Params<float> p;
-    int rc = make_params<float>(s, p, old, old);
-    if (rc) return rc;
-    const sbp::Band &bh = s->band_hb;
-    const long long tot = bh.nz_slab + bh.ny_slab + bh.nx_slab;
-    float **ns = reinterpret_cast<float **>(s->set[nw]);
-    SBP_CUDA(cudaEventRecord(s->ev_fork, s->stream));
-    SBP_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-    sbp::band_h<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->side>>>(p, bh, ns[3], ns[4], ns[5]);
-    SBP_CUDA(cudaGetLastError());
-    SBP_CUDA(cudaEventRecord(s->ev_join, s->side));
-    rc = launch_fused_interior_only(s);
-    if (rc) return rc;
-    SBP_CUDA(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
-    return SBP_OK;
-}
-
-// Fused path, phase 2: band E from E^n (old) and H^{n+1/2} (new) into the new set.
-int launch_fused_phase2(sbp_sim *s)
+// Band E from E^n (old) and H^{n+1/2} (new) into the new set, on stream st.
+int launch_band_e(sbp_sim *s, cudaStream_t st)
 {
     const int old = s->cur, nw = s->cur ^ 1;
     sbp::Params<float> p;
     int rc = make_params<float>(s, p, old, nw);
     if (rc) return rc;
     const sbp::Band &be = s->band_eb;
-    const long long tot = be.nz_slab + be.ny_slab + be.nx_slab;
     float **ns = reinterpret_cast<float **>(s->set[nw]);
-    sbp::band_e<float, false><<<(unsigned)((tot + 255) / 256), 256, 0, s->stream>>>(p, be, ns[0], ns[1], ns[2]);
+    sbp::band_e<float, false><<<be.ctas, 256, 0, st>>>(p, be, ns[0], ns[1], ns[2]);
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
+}
+
+// Fused path, phase 1: the one-pass interior step on the main stream and,
+// beside it on the side stream, band H (old -> new) followed by band E when
+// `chain_e` (band E of a block whose interface partner is another block waits
+// for that partner's band H instead: phase 2).  Joined before returning.
+int launch_fused_phase1(sbp_sim *s, bool chain_e)
+{
+    const int old = s->cur, nw = s->cur ^ 1;
+    sbp::Params<float> p;
+    int rc = make_params<float>(s, p, old, old);
+    if (rc) return rc;
+    const sbp::Band &bh = s->band_hb;
+    float **ns = reinterpret_cast<float **>(s->set[nw]);
+    SBP_CUDA(cudaEventRecord(s->ev_fork, s->stream));
+    rc = launch_fused_interior_only(s);
+    if (rc) return rc;
+    SBP_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
+    sbp::band_h<float, false><<<bh.ctas, 256, 0, s->side>>>(p, bh, ns[3], ns[4], ns[5]);
+    SBP_CUDA(cudaGetLastError());
+    if (chain_e && (rc = launch_band_e(s, s->side))) return rc;
+    SBP_CUDA(cudaEventRecord(s->ev_join, s->side));
+    SBP_CUDA(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
+    return SBP_OK;
+}
+
+// Fused path, phase 2 (blocks joined to another block): band E on the main stream.
+int launch_fused_phase2(sbp_sim *s) { return launch_band_e(s, s->stream); }
+
+// True when an interface face of s joins it to a block other than itself.
+bool linked_to_other(const sbp_sim *s)
+{
+    for (int f = 0; f < 6; f++)
+        if (s->face[f] == SBP_INTERFACE && s->nbr[f] && s->nbr[f] != s) return true;
+    return false;
 }
 
 int finalize_energy(const sbp_sim *s, double *dst)
@@ -671,12 +704,13 @@ int step_group(sbp_sim **sims, int nsims, int64_t nsteps)
         }
         for (int q = 0; q < nsims; q++) {
             sbp_sim *s = sims[q];
-            rc = s->fused_step ? launch_fused_phase1(s) : half_h(&s, 1);
+            rc = s->fused_step ? launch_fused_phase1(s, !linked_to_other(s)) : half_h(&s, 1);
             if (rc) return rc;
         }
         for (int q = 0; q < nsims; q++) {
             sbp_sim *s = sims[q];
             if (s->fused_step) {
+                if (!linked_to_other(s)) continue;
                 rc = launch_fused_phase2(s);
                 if (rc) return rc;
             } else {
@@ -723,10 +757,9 @@ int step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, in
             sbp::Params<float> p;
             if ((rc = make_params<float>(s, p, old, old))) break;
             const sbp::Band &bh = s->band_hb;
-            const long long tot_h = bh.nz_slab + bh.ny_slab + bh.nx_slab;
             float **ns = reinterpret_cast<float **>(s->set[nw]);
             if ((rc = mark(2))) break;
-            sbp::band_h<float, false><<<(unsigned)((tot_h + 255) / 256), 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+            sbp::band_h<float, false><<<bh.ctas, 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
             if ((rc = mark(-1))) break;
             // fused_interior alone: reuse phase 1 with the band launch skipped
             if ((rc = mark(3))) break;
@@ -781,6 +814,8 @@ struct sbp_batch {
     };
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on (capture runs nothing)
+    cudaStream_t side = nullptr;        // band H -> band E beside the one-pass step
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
     std::vector<Member> m;
     sbp::BatchGrid *d_grids = nullptr;
@@ -862,8 +897,8 @@ int batch_rebuild(sbp_batch *b)
         G.tiles[0] = s->fused_grid.x; G.tiles[1] = s->fused_grid.y; G.tiles[2] = s->fused_grid.z;
         cnt[g] = s->step;
         const long long nfg = (long long)s->fused_grid.x * s->fused_grid.y * s->fused_grid.z;
-        const long long nhg = (G.bh.nz_slab + G.bh.ny_slab + G.bh.nx_slab + 255) / 256;
-        const long long neg = (G.be.nz_slab + G.be.ny_slab + G.be.nx_slab + 255) / 256;
+        const long long nhg = G.bh.ctas;
+        const long long neg = G.be.ctas;
         if ((long long)pf[g] + nfg > INT32_MAX || (long long)ph[g] + nhg > INT32_MAX || (long long)pe[g] + neg > INT32_MAX)
             return SBP_ECAPACITY;
         pf[g + 1] = pf[g] + (int)nfg;
@@ -888,11 +923,18 @@ int batch_launch_chunk(sbp_batch *b, long long K)
 {
     const int n = (int)b->m.size();
     const int *pf = b->d_pre, *ph = b->d_pre + (b->cap + 1), *pe = b->d_pre + 2 * (b->cap + 1);
+    // per step: the one-pass interior step on the batch stream, band H then
+    // band E beside it on the side stream (band E reads only band H's output,
+    // which includes the first interior H layer), joined before the next step
     for (long long o = 0; o < K; o++) {
-        if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->stream>>>(b->d_grids, ph, n, (int)o);
+        SBP_CUDA(cudaEventRecord(b->ev_fork, b->stream));
         if (b->nf > 0)
             sbp::fused_batched<<<b->nf, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(b->d_grids, pf, n, (int)o);
-        if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->stream>>>(b->d_grids, pe, n, (int)o);
+        SBP_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+        if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->side>>>(b->d_grids, ph, n, (int)o);
+        if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->side>>>(b->d_grids, pe, n, (int)o);
+        SBP_CUDA(cudaEventRecord(b->ev_join, b->side));
+        SBP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
     }
     sbp::batch_advance<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_grids, n, K);
     SBP_CUDA(cudaGetLastError());
@@ -1173,8 +1215,15 @@ int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
     cudaGetDevice(&b->device);
     int rc = set_fused_smem_attr();
     if (rc) { delete b; return rc; }
-    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         (void)cudaGetLastError();
+        if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+        if (b->side) cudaStreamDestroy(b->side);
+        if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+        if (b->ev_join) cudaEventDestroy(b->ev_join);
         delete b;
         return SBP_ECUDA;
     }
@@ -1270,6 +1319,9 @@ int sbp_batch_destroy(sbp_batch *b)
     cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->side) cudaStreamDestroy(b->side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     if (b->d_grids) cudaFree(b->d_grids);
     if (b->d_pre) cudaFree(b->d_pre);
     if (b->d_counters) cudaFree(b->d_counters);
