@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 BYTES_H = 36.0      # per cell: read E (3) + H (3), write H (3), FP32
 BYTES_E = 40.0      # per cell: read H (3) + E (3) + eps_r (1), write E (3), FP32
 BYTES_FUSED = 52.0  # per cell: read E (3) + H (3) + eps_r (1), write H (3) + E (3), FP32
+# FP16 field storage: the six fields move 2 bytes per value, eps_r stays FP32
+BYTES16 = {"h_update": 18.0, "e_update": 24.0, "band_h": 18.0, "band_e": 24.0, "fused_interior": 28.0}
 
 
 def parse():
@@ -45,7 +47,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["dielectric", "serve"], default="dielectric")
+    ap.add_argument("--workload", choices=["dielectric", "mixed", "serve"], default="dielectric",
+                    help="dielectric: the N^3 dielectric cube (default); mixed: the N^3 block with PMC x, "
+                         "PEC y, absorbing z faces and four dielectric spheres; serve: the request stream")
+    ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32",
+                    help="fp16: FP32 arithmetic with FP16 field storage")
     ap.add_argument("--requests", type=int, default=512, help="serving workload: number of requests")
     ap.add_argument("--rho", type=float, default=0.9, help="serving workload: offered load / plain throughput")
     ap.add_argument("--slots", type=int, default=32)
@@ -157,11 +163,18 @@ def run_ours(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    w = wl.dielectric(N=args.N, steps=args.steps)
+    if args.workload == "mixed":
+        w = wl.mixed_faces(N=args.N, steps=args.steps)
+        faces = "PMC x, PEC y, absorbing z"
+    else:
+        w = wl.dielectric(N=args.N, steps=args.steps)
+        faces = "PEC x6"
+    fp16 = args.precision == "fp16"
+    prec = sbpsat.FP32_FP16STORE if fp16 else sbpsat.FP32
     spec = w.blocks[0]
     cells = spec.n[0] * spec.n[1] * spec.n[2]
     stream = torch.cuda.current_stream()
-    sim = sbpsat.from_workload(w, stream=stream)[0]
+    sim = sbpsat.from_workload(w, stream=stream, precision=prec)[0]
     sim.reserve_probes(args.warmup + args.steps + min(args.steps, 400) + 8)
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -200,6 +213,8 @@ def run_ours(args):
     dom = max(times, key=lambda k: times[k][0] * times[k][1])
     tdom = times[dom][0]
     ucount, bpc = units[dom]
+    if fp16:
+        bpc = BYTES16[dom]
     achieved = bpc * ucount / (tdom * 1e-3) / 1e9
     launches_per_step = sum(c for _, c in times.values()) / nk
     sim.close()
@@ -212,7 +227,7 @@ def run_ours(args):
         out = torch.empty(pinned[2].shape, dtype=torch.float32).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = sbpsat.Sim(spec.n, spec.h, spec.faces, eps_r=spec.eps_r, cfl=w.cfl, stream=stream)
+        s2 = sbpsat.Sim(spec.n, spec.h, spec.faces, eps_r=spec.eps_r, cfl=w.cfl, stream=stream, precision=prec)
         for c in range(6):
             sbpsat._check(sbpsat.lib().sbp_set_field(s2.handle, c, pinned[c].data_ptr(), 0), "set")
         for src in spec.sources:
@@ -241,9 +256,10 @@ def run_ours(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": "PEC x6",
-                       "cfl": w.cfl, "precision": "FP32", "parallelism": f"replicas x{world}",
-                       "l2": "inputs_larger_than_l2 (~470 MB working set)"},
+            "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": faces,
+                       "cfl": w.cfl, "precision": "FP32 arithmetic, FP16 storage" if fp16 else "FP32",
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs_larger_than_l2 (working set %.0f MB)" % (cells * (28 if fp16 else 52) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": recorded_traffic(dom), "algorithmic_bytes_per_cell": bpc,

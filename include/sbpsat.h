@@ -48,6 +48,12 @@ extern "C" {
 #define SBP_EAGAIN (-9)          /* result not ready yet (server poll)               */
 
 typedef enum { SBP_PEC = 0, SBP_PMC = 1, SBP_ABSORBING = 2, SBP_INTERFACE = 3 } sbp_face_t;
+/* Precision of a simulation.  SBP_FP32: FP32 fields and arithmetic (the
+ * material coefficients carried as double-float pairs).  SBP_FP64: FP64
+ * throughout.  SBP_FP32_FP16STORE: FP32 arithmetic, the six fields stored in
+ * FP16 as value / field_scale (rounded to nearest after every update, the
+ * next update reading the rounded value); eps_r and mu_r stay FP32.  The FP64
+ * energy (Eq. (16)) is always summed in FP64 from the stored fields. */
 typedef enum { SBP_FP32 = 0, SBP_FP64 = 1, SBP_FP32_FP16STORE = 2 } sbp_precision_t;
 typedef enum { SBP_EX = 0, SBP_EY = 1, SBP_EZ = 2, SBP_HX = 3, SBP_HY = 4, SBP_HZ = 5 } sbp_comp_t;
 typedef enum { SBP_GAUSS = 0, SBP_GAUSS_DERIV = 1, SBP_MOD_GAUSS = 2 } sbp_waveform_t;
@@ -73,6 +79,12 @@ typedef struct sbp_grid_desc {
     int32_t energy_every;    /* >0: compute the FP64 energy every that many steps during
                                 sbp_step and flag growth (sbp_energy_series); 0 = off      */
     int32_t flags;           /* SBP_FLAG_*                                                  */
+    double field_scale[2];   /* SBP_FP32_FP16STORE only: the stored FP16 value of a field is
+                                value / scale, one scale for E (V/m) and one for H (A/m);
+                                0 selects the default (E: 1, H: 1/eta0, so that eta0*H is
+                                stored).  Choose them so the largest field magnitude
+                                divided by its scale stays well below 65504.  Ignored for
+                                the other precisions.  Must be >= 0 and finite.           */
 } sbp_grid_desc;
 
 typedef struct sbp_sim sbp_sim;

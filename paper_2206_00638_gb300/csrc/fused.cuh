@@ -29,23 +29,40 @@ namespace sbp {
 
 constexpr int kFTX = 64;                 // H footprint width
 constexpr int kFTY = 8;                  // H footprint rows (= warps)
-constexpr int kFBX = kFTX + 4;           // TMA box width: x0-1 .. x0+63 from a 4-aligned start
 #ifndef SBP_FUSED_STAGES
 #define SBP_FUSED_STAGES 4
 #endif
 constexpr int kStages = SBP_FUSED_STAGES;     // TMA pipeline depth (planes in shared memory)
 constexpr int kERows = kFTY + 1;         // E rows y0-1 .. y0+7
 constexpr int kHRows = kFTY;             // H / eps rows y0 .. y0+7
-constexpr int kEField = 640;             // floats per E box slot (9*68 = 612, 128-byte rounded)
-constexpr int kHField = 576;             // floats per H / eps box slot (8*68 = 544, rounded)
-constexpr int kStageFloats = 3 * kEField + 4 * kHField;
-constexpr int kStageBytesTx = (3 * kERows * kFBX + 4 * kHRows * kFBX) * 4;   // bytes the TMA delivers
 constexpr int kHbufFloats = 2 * 3 * kFTY * kFTX;
-constexpr int kFusedSmem = (kStages * kStageFloats + kHbufFloats) * 4 + kStages * 8;
 constexpr unsigned kWaitLimit = 1u << 22;
 
-struct FusedParams {
-    float *out[6];                       // new set: element (i,j,k) at k*sz + j*sy + i
+constexpr int round128(int bytes) { return (bytes + 127) / 128 * 128; }
+
+// Shared-memory geometry of one pipeline stage for field storage type S.  A
+// TMA box starts at an x that is a multiple of 16 bytes (4 FP32 or 8 FP16
+// elements) at or below x0-1 and spans the 64 columns after it: kBX columns.
+// The eps box (always FP32) uses the same start and width.
+template <typename S>
+struct FusedGeom {
+    static constexpr int kAlign = 16 / (int)sizeof(S);
+    static constexpr int kBX = kFTX + kAlign;
+    static constexpr int kEBytes = round128(kERows * kBX * (int)sizeof(S));   // one E box slot
+    static constexpr int kHBytes = round128(kHRows * kBX * (int)sizeof(S));   // one H box slot
+    static constexpr int kPBytes = round128(kHRows * kBX * 4);                // the eps box slot
+    static constexpr int kStageBytes = 3 * kEBytes + 3 * kHBytes + kPBytes;
+    static constexpr int kTxBytes = (3 * kERows + 3 * kHRows) * kBX * (int)sizeof(S) + kHRows * kBX * 4;
+    static constexpr int kSmem = kStages * kStageBytes + kHbufFloats * 4 + kStages * 8;
+};
+constexpr int kFBX = FusedGeom<float>::kBX;
+constexpr int kFusedSmem = FusedGeom<float>::kSmem;
+constexpr int kFusedSmemH = FusedGeom<__half>::kSmem;
+
+template <typename S>
+struct FusedParamsT {
+    S *out[6];                           // new set: element (i,j,k) at k*sz + j*sy + i
+    float pscale[2];                     // probe value = stored value * pscale[E=0 / H=1]
     int n[3];
     long long sy, sz;
     Coef<float> B[3], A[3], AJ;
@@ -58,6 +75,7 @@ struct FusedParams {
     int kchunk;
     int *error_flag;                     // set to 1 when a pipeline wait gives up
 };
+using FusedParams = FusedParamsT<float>;
 
 // --- mbarrier / TMA helpers (inline PTX) ----------------------------------
 __device__ __forceinline__ unsigned smem_addr(const void *p)
@@ -103,24 +121,37 @@ struct FusedMaps {
     CUtensorMap e[3], h[3], eps;
 };
 
-__device__ __forceinline__ void issue_plane(const FusedMaps &m, float *stage, uint64_t *bar, int xb, int y0, int plane)
+template <typename S>
+__device__ __forceinline__ void issue_plane(const FusedMaps &m, unsigned char *stage, uint64_t *bar, int xb, int y0,
+                                            int plane)
 {
-    mbar_expect_tx(bar, kStageBytesTx);
+    using Gm = FusedGeom<S>;
+    mbar_expect_tx(bar, Gm::kTxBytes);
 #pragma unroll
-    for (int f = 0; f < 3; ++f) tma_load_3d(stage + f * kEField, &m.e[f], xb, y0 - 1, plane, bar);
+    for (int f = 0; f < 3; ++f) tma_load_3d(stage + f * Gm::kEBytes, &m.e[f], xb, y0 - 1, plane, bar);
 #pragma unroll
-    for (int f = 0; f < 3; ++f) tma_load_3d(stage + 3 * kEField + f * kHField, &m.h[f], xb, y0, plane, bar);
-    tma_load_3d(stage + 3 * kEField + 3 * kHField, &m.eps, xb, y0, plane, bar);
+    for (int f = 0; f < 3; ++f) tma_load_3d(stage + 3 * Gm::kEBytes + f * Gm::kHBytes, &m.h[f], xb, y0, plane, bar);
+    tma_load_3d(stage + 3 * Gm::kEBytes + 3 * Gm::kHBytes, &m.eps, xb, y0, plane, bar);
 }
 
 // One CTA of the one-pass interior step: tile (bx, by) in x/y, z-chunk bz,
 // time step `step` (J is evaluated at t^{step+1/2}), probe sample `pslot`.
-template <bool SRC>
-__device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedParams &p, long long step, long long pslot,
-                                           int bx, int by, int bz, float *smem)
+template <bool SRC, typename S>
+__device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedParamsT<S> &p, long long step,
+                                           long long pslot, int bx, int by, int bz, unsigned char *smem)
 {
-    float *hbuf = smem + kStages * kStageFloats;
+    using Gm = FusedGeom<S>;
+    constexpr int kBX = Gm::kBX;
+    float *hbuf = reinterpret_cast<float *>(smem + kStages * Gm::kStageBytes);
     uint64_t *bar = reinterpret_cast<uint64_t *>(hbuf + kHbufFloats);
+    // slots of a stage: E fields, H fields (storage type), eps (FP32)
+    auto slotE = [&](int st, int f) { return reinterpret_cast<const S *>(smem + st * Gm::kStageBytes + f * Gm::kEBytes); };
+    auto slotH = [&](int st, int f) {
+        return reinterpret_cast<const S *>(smem + st * Gm::kStageBytes + 3 * Gm::kEBytes + f * Gm::kHBytes);
+    };
+    auto slotP = [&](int st) {
+        return reinterpret_cast<const float *>(smem + st * Gm::kStageBytes + 3 * Gm::kEBytes + 3 * Gm::kHBytes);
+    };
 
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
@@ -128,8 +159,8 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     const int y0 = 3 + by * (kFTY - 1);
     const int k0 = 3 + bz * p.kchunk;
     const int k1 = min(k0 + p.kchunk, nz - 2);       // E planes [k0, k1); H planes [k0, k1]
-    const int xb = (x0 - 1) & ~3;
-    const int cx0 = x0 - xb;                          // smem column of x0, in 1..4
+    const int xb = (x0 - 1) & ~(Gm::kAlign - 1);
+    const int cx0 = x0 - xb;                          // smem column of x0, in 1..kAlign
     const int nplanes = k1 - k0 + 2;                  // planes k0-1 .. k1 are loaded
     const int j = y0 + w;
 
@@ -141,7 +172,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     int issued = 0;                                   // planes issued (thread 0's count)
     if (threadIdx.x == 0)
         for (; issued < kStages && issued < nplanes; ++issued)
-            issue_plane(maps, smem + issued * kStageFloats, &bar[issued], xb, y0, k0 - 1 + issued);
+            issue_plane<S>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
 
     // per-thread probe / source masks for the two columns
     unsigned long long pmask[2] = {0ull, 0ull};
@@ -181,15 +212,15 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0); waited = 1; }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int re = (w + 1) * kFBX + cx0 + lane + 32 * h;
+        const int re = (w + 1) * kBX + cx0 + lane + 32 * h;
 #pragma unroll
-        for (int f = 0; f < 3; ++f) { ec[h][f] = smem[f * kEField + re]; hc[h][f] = 0.f; }
+        for (int f = 0; f < 3; ++f) { ec[h][f] = ld_s(slotE(0, f) + re); hc[h][f] = 0.f; }
 #pragma unroll
         for (int f = 0; f < 3; ++f) epc[h][f] = 0.f;
     }
     if (__syncthreads_or(!ok)) aborted = true;
     if (!aborted && threadIdx.x == 0 && kStages < nplanes) {   // plane k0-1 is in registers now
-        issue_plane(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
+        issue_plane<S>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
         ++issued;
     }
     for (int q = k0; q <= k1 && !aborted; ++q) {
@@ -197,7 +228,9 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         const int sq = iq % kStages;
         if (ok) ok = mbar_wait_bounded(&bar[sq], (iq / kStages) & 1);
         waited = iq + 1;
-        const float *Sq = smem + sq * kStageFloats;   // plane q
+        const S *E0 = slotE(sq, 0), *E1 = slotE(sq, 1), *E2 = slotE(sq, 2);   // plane q
+        const S *H0 = slotH(sq, 0), *H1 = slotH(sq, 1), *H2 = slotH(sq, 2);
+        const float *eq = slotP(sq);
         float *Hq = hbuf + (q & 1) * (3 * kFTY * kFTX);
         const float *Hp = hbuf + ((q - 1) & 1) * (3 * kFTY * kFTX);
         const bool doE = q > k0;
@@ -208,26 +241,28 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             const int c = lane + 32 * h;
             const int cc = cx0 + c;
             // ---- H^{n+1/2} at (i, j, q) --------------------------------------
-            const int re = (w + 1) * kFBX + cc;           // E slot row of j
-            const int rh = w * kFBX + cc;                 // H slot row of j
-            const float exq = Sq[0 * kEField + re], ex_jm = Sq[0 * kEField + re - kFBX];
-            const float eyq = Sq[1 * kEField + re], ey_im = Sq[1 * kEField + re - 1];
-            const float ezq = Sq[2 * kEField + re], ez_im = Sq[2 * kEField + re - 1], ez_jm = Sq[2 * kEField + re - kFBX];
+            const int re = (w + 1) * kBX + cc;            // E slot row of j
+            const int rh = w * kBX + cc;                  // H slot row of j
+            const float exq = ld_s(E0 + re), ex_jm = ld_s(E0 + re - kBX);
+            const float eyq = ld_s(E1 + re), ey_im = ld_s(E1 + re - 1);
+            const float ezq = ld_s(E2 + re), ez_im = ld_s(E2 + re - 1), ez_jm = ld_s(E2 + re - kBX);
             Acc<float> bx, by, bz;
             bx.add(Bz, eyq - ec[h][1]); bx.add(By, ezq - ez_jm, -1.f);
             by.add(Bx, ezq - ez_im);    by.add(Bz, exq - ec[h][0], -1.f);
             bz.add(By, exq - ex_jm);    bz.add(Bx, eyq - ey_im, -1.f);
-            const float hx = Sq[3 * kEField + 0 * kHField + rh] + plain_increment(bx);
-            const float hy = Sq[3 * kEField + 1 * kHField + rh] + plain_increment(by);
-            const float hz = Sq[3 * kEField + 2 * kHField + rh] + plain_increment(bz);
+            // the values the stores keep (FP16 storage rounds here, and E
+            // below uses the rounded H, as a separate E half-step would)
+            const float hx = quant<S>(ld_s(H0 + rh) + plain_increment(bx));
+            const float hy = quant<S>(ld_s(H1 + rh) + plain_increment(by));
+            const float hz = quant<S>(ld_s(H2 + rh) + plain_increment(bz));
             Hq[(0 * kFTY + w) * kFTX + c] = hx;
             Hq[(1 * kFTY + w) * kFTX + c] = hy;
             Hq[(2 * kFTY + w) * kFTX + c] = hz;
             if (colH[h] && (q < k1 || q == nz - 2)) {
                 const long long o = (long long)q * p.sz + obase[h];
-                p.out[3][o] = hx;
-                p.out[4][o] = hy;
-                p.out[5][o] = hz;
+                st_s(p.out[3] + o, hx);
+                st_s(p.out[4] + o, hy);
+                st_s(p.out[5] + o, hz);
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
@@ -235,14 +270,14 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                         m &= m - 1;
                         const Prb &P = p.prb[b];
                         if (P.k == q && P.comp >= 3 && pslot < p.probe_cap)
-                            p.probe_buf[(long long)b * p.probe_cap + pslot] = P.comp == 3 ? hx : P.comp == 4 ? hy : hz;
+                            p.probe_buf[(long long)b * p.probe_cap + pslot] =
+                                (P.comp == 3 ? hx : P.comp == 4 ? hy : hz) * p.pscale[1];
                     }
                 }
             }
             // eps cells of plane q (rows j, j+1; columns i, i+1), as the pair sums
             // the node sums of cell_sum are built from: (a+b)+(c+d)
-            const float *eq = Sq + 3 * kEField + 3 * kHField;
-            const int r0 = w * kFBX + cc, r1 = r0 + kFBX;
+            const int r0 = w * kBX + cc, r1 = r0 + kBX;
             const float q00 = eq[r0], q01 = eq[r1], q10 = eq[r0 + 1], q11 = eq[r1 + 1];
             const float qa = q00 + q01, qb = q00 + q10, qc = q01 + q11;
 
@@ -268,22 +303,22 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                     while (m) {
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        const Src &S = p.src[b];
-                        if (S.k < 0 || S.k == pl) {
-                            const float J = (float)(S.amp * waveform(S.wf, t_half, S.tw, S.t0, S.f));
-                            if (S.comp == 0) ax.add(p.AJ, J, -1.f);
-                            else if (S.comp == 1) ay.add(p.AJ, J, -1.f);
+                        const Src &Sr = p.src[b];
+                        if (Sr.k < 0 || Sr.k == pl) {
+                            const float J = (float)(Sr.amp * waveform(Sr.wf, t_half, Sr.tw, Sr.t0, Sr.f));
+                            if (Sr.comp == 0) ax.add(p.AJ, J, -1.f);
+                            else if (Sr.comp == 1) ay.add(p.AJ, J, -1.f);
                             else az.add(p.AJ, J, -1.f);
                         }
                     }
                 }
-                const float ex = ec[h][0] + scaled_increment(ax, sx);
-                const float ey = ec[h][1] + scaled_increment(ay, sy);
-                const float ez = ec[h][2] + scaled_increment(az, sz);
+                const float ex = quant<S>(ec[h][0] + scaled_increment(ax, sx));
+                const float ey = quant<S>(ec[h][1] + scaled_increment(ay, sy));
+                const float ez = quant<S>(ec[h][2] + scaled_increment(az, sz));
                 const long long o = (long long)pl * p.sz + obase[h];
-                p.out[0][o] = ex;
-                p.out[1][o] = ey;
-                p.out[2][o] = ez;
+                st_s(p.out[0] + o, ex);
+                st_s(p.out[1] + o, ey);
+                st_s(p.out[2] + o, ez);
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
@@ -291,7 +326,8 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                         m &= m - 1;
                         const Prb &P = p.prb[b];
                         if (P.k == pl && P.comp < 3 && pslot < p.probe_cap)
-                            p.probe_buf[(long long)b * p.probe_cap + pslot] = P.comp == 0 ? ex : P.comp == 1 ? ey : ez;
+                            p.probe_buf[(long long)b * p.probe_cap + pslot] =
+                                (P.comp == 0 ? ex : P.comp == 1 ? ey : ez) * p.pscale[0];
                     }
                 }
             }
@@ -305,7 +341,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         if (threadIdx.x == 0) {
             const int nxt = q + kStages;
             if (nxt <= k1) {
-                issue_plane(maps, smem + sq * kStageFloats, &bar[sq], xb, y0, nxt);
+                issue_plane<S>(maps, smem + sq * Gm::kStageBytes, &bar[sq], xb, y0, nxt);
                 ++issued;
             }
         }
@@ -319,11 +355,12 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     }
 }
 
-template <bool SRC>
-__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_interior(const __grid_constant__ FusedMaps maps, const FusedParams p)
+template <bool SRC, typename S>
+__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2)
+    fused_interior(const __grid_constant__ FusedMaps maps, const FusedParamsT<S> p)
 {
-    extern __shared__ __align__(128) float smem[];
-    fused_body<SRC>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    fused_body<SRC, S>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,8 +448,8 @@ __device__ __forceinline__ unsigned long long warp_probe_mask(const Prb *prb, in
     return m;
 }
 
-template <typename T>
-__device__ __forceinline__ void band_probes(const Params<T> &p, unsigned long long m, int c0, int i, int j,
+template <typename T, typename S>
+__device__ __forceinline__ void band_probes(const Params<T, S> &p, unsigned long long m, int c0, int i, int j,
                                             long long pslot, const T v[3], const bool have[3])
 {
     while (m) {
@@ -422,31 +459,31 @@ __device__ __forceinline__ void band_probes(const Params<T> &p, unsigned long lo
         const int c = P.comp - c0;
         const bool hv = c == 0 ? have[0] : c == 1 ? have[1] : have[2];
         if (P.i == i && P.j == j && hv && pslot < p.probe_cap)
-            p.probe_buf[(long long)q * p.probe_cap + pslot] = c == 0 ? v[0] : c == 1 ? v[1] : v[2];
+            p.probe_buf[(long long)q * p.probe_cap + pslot] = (c == 0 ? v[0] : c == 1 ? v[1] : v[2]) * p.fscale[c0 >= 3];
     }
 }
 
 // H^{n+1/2} at one band node, closure axes G: every load first (in bounds for
 // all three components: the node and its row entries lie in the padded
 // layout), then the updates.
-template <typename T, bool MUVAR, int G>
-__device__ __forceinline__ void band_h_at(const Params<T> &p, const int idx[3], long long o, const bool have[3],
-                                          T *const outs[3], T hn[3])
+template <typename T, bool MUVAR, int G, typename S>
+__device__ __forceinline__ void band_h_at(const Params<T, S> &p, const int idx[3], long long o, const bool have[3],
+                                          S *const outs[3], T hn[3])
 {
     Tri<T> vx[2], vy[2], vz[2];
     h_gather<T, 3, G>(p, idx, o, vx);
     h_gather<T, 4, G>(p, idx, o, vy);
     h_gather<T, 5, G>(p, idx, o, vz);
-    const T hx = p.F[3][o], hy = p.F[4][o], hz = p.F[5][o];
-    if (have[0]) outs[0][o] = hn[0] = h_apply<T, 3, MUVAR, G>(p, idx, o, hx, vx);
-    if (have[1]) outs[1][o] = hn[1] = h_apply<T, 4, MUVAR, G>(p, idx, o, hy, vy);
-    if (have[2]) outs[2][o] = hn[2] = h_apply<T, 5, MUVAR, G>(p, idx, o, hz, vz);
+    const T hx = ld_s(p.F[3] + o), hy = ld_s(p.F[4] + o), hz = ld_s(p.F[5] + o);
+    if (have[0]) st_s(outs[0] + o, hn[0] = quant<S>(h_apply<T, 3, MUVAR, G>(p, idx, o, hx, vx)));
+    if (have[1]) st_s(outs[1] + o, hn[1] = quant<S>(h_apply<T, 4, MUVAR, G>(p, idx, o, hy, vy)));
+    if (have[2]) st_s(outs[2] + o, hn[2] = quant<S>(h_apply<T, 5, MUVAR, G>(p, idx, o, hz, vz)));
 }
 
 // H^{n+1/2} at the nodes of band warp w: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
-template <typename T, bool MUVAR>
-__device__ __forceinline__ void band_h_warp(const Params<T> &p, const Band &b, unsigned w, int lane, long long pslot,
-                                            T *const outs[3])
+template <typename T, bool MUVAR, typename S>
+__device__ __forceinline__ void band_h_warp(const Params<T, S> &p, const Band &b, unsigned w, int lane, long long pslot,
+                                            S *const outs[3])
 {
     int i, j, k, il, ih, jl, jh, G;
     const bool valid = band_lane(b, p.n, w, lane, i, j, k, il, ih, jl, jh, G);
@@ -468,37 +505,37 @@ __device__ __forceinline__ void band_h_warp(const Params<T> &p, const Band &b, u
     if (pm) band_probes(p, pm, 3, i, j, pslot, hn, have);
 }
 
-template <typename T, bool MUVAR>
-__global__ void __launch_bounds__(256) band_h(const Params<T> p, const Band b, T *hx_out, T *hy_out, T *hz_out)
+template <typename T, bool MUVAR, typename S>
+__global__ void __launch_bounds__(256) band_h(const Params<T, S> p, const Band b, S *hx_out, S *hy_out, S *hz_out)
 {
     const unsigned w = blockIdx.x * 8u + (threadIdx.x >> 5);
     if (w >= b.wz + b.wy + b.wx) return;
-    T *const outs[3] = {hx_out, hy_out, hz_out};
+    S *const outs[3] = {hx_out, hy_out, hz_out};
     band_h_warp<T, MUVAR>(p, b, w, threadIdx.x & 31, p.probe_slot, outs);
 }
 
 // E^{n+1} at one band node, closure axes G (see band_h_at).
-template <typename T, bool MUVAR, int G>
-__device__ __forceinline__ void band_e_at(const Params<T> &p, const int idx[3], long long o, const bool have[3],
-                                          unsigned sm, double t_half, T *const outs[3], T en[3])
+template <typename T, bool MUVAR, int G, typename S>
+__device__ __forceinline__ void band_e_at(const Params<T, S> &p, const int idx[3], long long o, const bool have[3],
+                                          unsigned sm, double t_half, S *const outs[3], T en[3])
 {
     Tri<T> vx[2], vy[2], vz[2];
     e_gather<T, 0, false, G>(p, idx, o, vx);
     e_gather<T, 1, false, G>(p, idx, o, vy);
     e_gather<T, 2, false, G>(p, idx, o, vz);
-    const T ex = p.F[0][o], ey = p.F[1][o], ez = p.F[2][o];
+    const T ex = ld_s(p.F[0] + o), ey = ld_s(p.F[1] + o), ez = ld_s(p.F[2] + o);
     const T sx = cell_sum<0, T>(p.eps, o, p.sy, p.sz);
     const T sy = cell_sum<1, T>(p.eps, o, p.sy, p.sz);
     const T sz = cell_sum<2, T>(p.eps, o, p.sy, p.sz);
-    if (have[0]) outs[0][o] = en[0] = e_apply<T, 0, MUVAR, false, G>(p, idx, o, ex, sx, vx, sm, t_half);
-    if (have[1]) outs[1][o] = en[1] = e_apply<T, 1, MUVAR, false, G>(p, idx, o, ey, sy, vy, sm, t_half);
-    if (have[2]) outs[2][o] = en[2] = e_apply<T, 2, MUVAR, false, G>(p, idx, o, ez, sz, vz, sm, t_half);
+    if (have[0]) st_s(outs[0] + o, en[0] = quant<S>(e_apply<T, 0, MUVAR, false, G>(p, idx, o, ex, sx, vx, sm, t_half)));
+    if (have[1]) st_s(outs[1] + o, en[1] = quant<S>(e_apply<T, 1, MUVAR, false, G>(p, idx, o, ey, sy, vy, sm, t_half)));
+    if (have[2]) st_s(outs[2] + o, en[2] = quant<S>(e_apply<T, 2, MUVAR, false, G>(p, idx, o, ez, sz, vz, sm, t_half)));
 }
 
 // E^{n+1} at the nodes of band warp w: p.F = {E^n (old), H^{n+1/2} (new)}, outs = new E.
-template <typename T, bool MUVAR>
-__device__ __forceinline__ void band_e_warp(const Params<T> &p, const Band &b, unsigned w, int lane, long long step,
-                                            long long pslot, T *const outs[3])
+template <typename T, bool MUVAR, typename S>
+__device__ __forceinline__ void band_e_warp(const Params<T, S> &p, const Band &b, unsigned w, int lane, long long step,
+                                            long long pslot, S *const outs[3])
 {
     int i, j, k, il, ih, jl, jh, G;
     const bool valid = band_lane(b, p.n, w, lane, i, j, k, il, ih, jl, jh, G);
@@ -508,9 +545,9 @@ __device__ __forceinline__ void band_e_warp(const Params<T> &p, const Band &b, u
     if (p.nsrc) {
         bool hit = false;
         if (lane < p.nsrc) {
-            const Src &S = p.src[lane];
-            hit = (S.i < 0 || (S.i >= il && S.i <= ih)) && (S.j < 0 || (S.j >= jl && S.j <= jh)) &&
-                  (S.k < 0 || S.k == k);
+            const Src &Sr = p.src[lane];
+            hit = (Sr.i < 0 || (Sr.i >= il && Sr.i <= ih)) && (Sr.j < 0 || (Sr.j >= jl && Sr.j <= jh)) &&
+                  (Sr.k < 0 || Sr.k == k);
         }
         wm = __ballot_sync(0xffffffffu, hit);
     }
@@ -537,12 +574,12 @@ __device__ __forceinline__ void band_e_warp(const Params<T> &p, const Band &b, u
     if (pm) band_probes(p, pm, 0, i, j, pslot, en, have);
 }
 
-template <typename T, bool MUVAR>
-__global__ void __launch_bounds__(256) band_e(const Params<T> p, const Band b, T *ex_out, T *ey_out, T *ez_out)
+template <typename T, bool MUVAR, typename S>
+__global__ void __launch_bounds__(256) band_e(const Params<T, S> p, const Band b, S *ex_out, S *ey_out, S *ez_out)
 {
     const unsigned w = blockIdx.x * 8u + (threadIdx.x >> 5);
     if (w >= b.wz + b.wy + b.wx) return;
-    T *const outs[3] = {ex_out, ey_out, ez_out};
+    S *const outs[3] = {ex_out, ey_out, ez_out};
     band_e_warp<T, MUVAR>(p, b, w, threadIdx.x & 31, p.step, p.probe_slot, outs);
 }
 
@@ -592,7 +629,7 @@ __device__ __forceinline__ bool batch_state(const BatchGrid &g, int offset, long
 __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_batched(const BatchGrid *G, const int *pre, int n,
                                                                                   int offset)
 {
-    extern __shared__ __align__(128) float smem[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int g = find_slot(pre, n, blockIdx.x);
     const BatchGrid &B = G[g];
     long long step;
@@ -600,8 +637,8 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_batched
     if (!batch_state(B, offset, step, par)) return;
     const int local = blockIdx.x - pre[g];
     const int tx = B.tiles[0], ty = B.tiles[1];
-    fused_body<true>(B.maps[par], B.fp[par], step, step - B.probe_base, local % tx, (local / tx) % ty, local / (tx * ty),
-                     smem);
+    fused_body<true, float>(B.maps[par], B.fp[par], step, step - B.probe_base, local % tx, (local / tx) % ty,
+                            local / (tx * ty), smem_raw);
 }
 
 __global__ void __launch_bounds__(256) band_h_batched(const BatchGrid *G, const int *pre, int n, int offset)

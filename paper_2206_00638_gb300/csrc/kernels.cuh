@@ -19,6 +19,8 @@
 // so rounding of a coefficient does not bias the phase velocity; only the
 // per-step rounding of the field update (unbiased) remains.
 #pragma once
+#include <cuda_fp16.h>
+
 #include <cstdint>
 #include <type_traits>
 
@@ -65,9 +67,19 @@ struct Link {               // interface partner of one face
 struct Src { int comp, i, j, k, wf; double amp, tw, t0, f; };
 struct Prb { int comp, i, j, k; };
 
-template <typename T>
+// Field storage type S and the arithmetic type of its values: FP16 storage
+// is computed in FP32.
+template <typename S> struct Compute { using type = S; };
+template <> struct Compute<__half> { using type = float; };
+template <typename S> using compute_t = typename Compute<S>::type;
+
+// T: arithmetic type; S: storage type of the six fields (T, or __half with
+// T = float).  Stored FP16 values are field / scale, one scale for E and one
+// for H; the curl coefficients below carry the ratio of the two scales, so a
+// kernel only converts on load and store.
+template <typename T, typename S = T>
 struct Params {
-    T *F[6];                // padded fields Ex..Hz: element (i,j,k) at k*sz + j*sy + i
+    S *F[6];                // padded fields Ex..Hz: element (i,j,k) at k*sz + j*sy + i
     const float *eps;       // ghost-padded cell eps_r on the same layout: cell (cx,cy,cz) at (cx+1,cy+1,cz+1)
     const float *mu;        // same for mu_r (only read when MUVAR)
     int n[3];
@@ -82,6 +94,9 @@ struct Params {
     int nsrc, nprb;
     Src src[kMaxSources];
     Prb prb[kMaxProbes];
+    T fscale[2];                       // physical value = stored value * fscale[E=0 / H=1]
+    T uB, uA;                          // fscale[H]/fscale[E] and its inverse: B and A carry the
+                                       // scale ratio; the absorbing-SAT gamma needs them without
     T *probe_buf;
     long long probe_cap, probe_slot;   // sample slot of this step (skip if >= cap)
     long long step;                    // n: the E half-step injects J(t^{n+1/2})
@@ -140,21 +155,51 @@ __device__ __forceinline__ double plain_increment(const Acc<double> &a) { return
 // padded layout, so the gathered triple is always in bounds.
 template <typename T> struct Tri { T a, b, c; };
 
-// Field load; CG = true reads through L2 only (ld.global.cg), for values this
-// kernel itself wrote earlier (coherent across the threads of a CTA after a
-// barrier, never served stale from L1 or the read-only path).
-template <bool CG, typename T>
-__device__ __forceinline__ T ldf(const T *p)
+// Field loads and stores in the storage type, values in the arithmetic type.
+template <typename S>
+__device__ __forceinline__ compute_t<S> ld_s(const S *p)
 {
-    if constexpr (CG) return __ldcg(p);
+    if constexpr (std::is_same<S, __half>::value) return __half2float(*p);
     else return *p;
+}
+template <typename S>
+__device__ __forceinline__ compute_t<S> ldg_s(const S *p)
+{
+    if constexpr (std::is_same<S, __half>::value) return __half2float(__ldg(p));
+    else return __ldg(p);
+}
+// CG = true reads through L2 only (ld.global.cg), for values this kernel
+// itself wrote earlier (coherent across the threads of a CTA after a
+// barrier, never served stale from L1 or the read-only path).
+template <bool CG, typename S>
+__device__ __forceinline__ compute_t<S> ldf(const S *p)
+{
+    if constexpr (CG) {
+        if constexpr (std::is_same<S, __half>::value) return __half2float(__ldcg(p));
+        else return __ldcg(p);
+    } else {
+        return ld_s(p);
+    }
+}
+// The value a store of v keeps (round to nearest for FP16 storage).
+template <typename S, typename T>
+__device__ __forceinline__ T quant(T v)
+{
+    if constexpr (std::is_same<S, __half>::value) return __half2float(__float2half_rn(v));
+    else return v;
+}
+template <typename S, typename T>
+__device__ __forceinline__ void st_s(S *p, T v)
+{
+    if constexpr (std::is_same<S, __half>::value) *p = __float2half_rn(v);
+    else *p = v;
 }
 
 // entries s0, s0+1, s0+2 of the line starting at `line` with stride s
-template <bool CG, typename T>
-__device__ __forceinline__ Tri<T> tri_load(const T *line, long long s, int s0)
+template <bool CG, typename S>
+__device__ __forceinline__ Tri<compute_t<S>> tri_load(const S *line, long long s, int s0)
 {
-    const T *q = line + (long long)s0 * s;
+    const S *q = line + (long long)s0 * s;
     return {ldf<CG>(q), ldf<CG>(q + s), ldf<CG>(q + 2 * s)};
 }
 
@@ -243,8 +288,8 @@ __device__ __forceinline__ double waveform(int wf, double t, double tw, double t
     return sin(6.283185307179586 * ph) * g;
 }
 
-template <typename T>
-__device__ __forceinline__ bool probe_here(const Params<T> &p, unsigned long long mask, int k)
+template <typename T, typename S>
+__device__ __forceinline__ bool probe_here(const Params<T, S> &p, unsigned long long mask, int k)
 {
     while (mask) {
         int q = __ffsll(mask) - 1;
@@ -253,8 +298,8 @@ __device__ __forceinline__ bool probe_here(const Params<T> &p, unsigned long lon
     }
     return false;
 }
-template <typename T>
-__device__ __forceinline__ bool source_here(const Params<T> &p, unsigned mask, int k)
+template <typename T, typename S>
+__device__ __forceinline__ bool source_here(const Params<T, S> &p, unsigned mask, int k)
 {
     while (mask) {
         int q = __ffs(mask) - 1;
@@ -263,14 +308,14 @@ __device__ __forceinline__ bool source_here(const Params<T> &p, unsigned mask, i
     }
     return false;
 }
-template <typename T>
-__device__ __forceinline__ void write_probes(const Params<T> &p, unsigned long long mask, int c, int k, T v)
+template <typename T, typename S>
+__device__ __forceinline__ void write_probes(const Params<T, S> &p, unsigned long long mask, int c, int k, T v)
 {
     while (mask) {
         int q = __ffsll(mask) - 1;
         mask &= mask - 1;
         if (p.prb[q].comp == c && p.prb[q].k == k && p.probe_slot < p.probe_cap)
-            p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = v;
+            p.probe_buf[(long long)q * p.probe_cap + p.probe_slot] = v * p.fscale[c >= 3];
     }
 }
 
@@ -297,8 +342,8 @@ __device__ __forceinline__ void block_sum_to(double v, double *dst)
 // Entries of E read by the two curl terms of H component C at node idx.
 // G: bit a set when the node may lie on a closure row or face along axis a;
 // along the other axes the node is interior and the row is u_r - u_{r-1}.
-template <typename T, int C, int G = 7>
-__device__ __forceinline__ void h_gather(const Params<T> &p, const int idx[3], long long o, Tri<T> v[2])
+template <typename T, int C, int G = 7, typename S = T>
+__device__ __forceinline__ void h_gather(const Params<T, S> &p, const int idx[3], long long o, Tri<T> v[2])
 {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -307,16 +352,16 @@ __device__ __forceinline__ void h_gather(const Params<T> &p, const int idx[3], l
         if ((G >> a) & 1) {
             v[t] = tri_load<false>(p.F[u] + (o - idx[a] * st), st, dminus_start(idx[a], p.n[a]));
         } else {
-            v[t].a = p.F[u][o - st];
-            v[t].b = p.F[u][o];
+            v[t].a = ld_s(p.F[u] + o - st);
+            v[t].b = ld_s(p.F[u] + o);
             v[t].c = v[t].b;
         }
     }
 }
 
 // H^{n+1/2} of component C at node idx from H^{n-1/2} (hold) and the gathered E.
-template <typename T, int C, bool MUVAR, int G = 7>
-__device__ __forceinline__ T h_apply(const Params<T> &p, const int idx[3], long long o, T hold, const Tri<T> v[2])
+template <typename T, int C, bool MUVAR, int G = 7, typename S = T>
+__device__ __forceinline__ T h_apply(const Params<T, S> &p, const int idx[3], long long o, T hold, const Tri<T> v[2])
 {
     Acc<T> acc;
     T gam = T(0);
@@ -342,16 +387,16 @@ __device__ __forceinline__ T h_apply(const Params<T> &p, const int idx[3], long 
                     const T mr = MUVAR ? cell_sum<C, T>(p.mu, o, p.sy, p.sz) * T(0.5) : T(1);
                     const T eta = T(p.eta0) * sqrt(mr / er);
                     // gamma = dt eta / (2 mu h_a); B holds dt/(mu0 h_a) (x2 when mu varies)
-                    const T ba = MUVAR ? T(p.B[a].hi) * T(0.5) / mr : T(p.B[a].hi);
+                    const T ba = (MUVAR ? T(p.B[a].hi) * T(0.5) / mr : T(p.B[a].hi)) * p.uB;
                     gam += T(0.5) * ba * eta;
                 } else {   // interface: (phi/2)(E^A - E^B) / (mu w), w = h/2
                     const Link &L = p.link[f];
-                    const T *nf = static_cast<const T *>(L.F[u]);
+                    const S *nf = static_cast<const S *>(L.F[u]);
                     const int nidx = L.side < 0 ? 0 : L.n_norm;      // partner E on its plus grid along a
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
                     for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
-                    acc.add(p.B[a], pv - nf[on], phi);
+                    acc.add(p.B[a], pv - ld_s(nf + on), phi);
                 }
             }
         }
@@ -367,18 +412,18 @@ __device__ __forceinline__ T h_apply(const Params<T> &p, const int idx[3], long 
 }
 
 // H half-step, general path, one component at one node (Eqs. (10)-(15)).
-template <typename T, int C, bool MUVAR>
-__device__ __forceinline__ T h_node(const Params<T> &p, const int idx[3], long long o, T hold)
+template <typename T, int C, bool MUVAR, typename S = T>
+__device__ __forceinline__ T h_node(const Params<T, S> &p, const int idx[3], long long o, T hold)
 {
     Tri<T> v[2];
-    h_gather<T, C>(p, idx, o, v);
-    return h_apply<T, C, MUVAR>(p, idx, o, hold, v);
+    h_gather<T, C, 7>(p, idx, o, v);
+    return h_apply<T, C, MUVAR, 7>(p, idx, o, hold, v);
 }
 
 // Entries of H read by the two curl terms of E component C at node idx.
 // G as for h_gather; interior rows of D+ are v_{r+1} - v_r.
-template <typename T, int C, bool CG = false, int G = 7>
-__device__ __forceinline__ void e_gather(const Params<T> &p, const int idx[3], long long o, Tri<T> v[2])
+template <typename T, int C, bool CG = false, int G = 7, typename S = T>
+__device__ __forceinline__ void e_gather(const Params<T, S> &p, const int idx[3], long long o, Tri<T> v[2])
 {
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -396,8 +441,8 @@ __device__ __forceinline__ void e_gather(const Params<T> &p, const int idx[3], l
 
 // E^{n+1} of component C at node idx from E^n (eold), se = sum4 eps_r of the
 // node and the gathered H.
-template <typename T, int C, bool MUVAR, bool CG = false, int G = 7>
-__device__ __forceinline__ T e_apply(const Params<T> &p, const int idx[3], long long o, T eold, T se, const Tri<T> v[2],
+template <typename T, int C, bool MUVAR, bool CG = false, int G = 7, typename S = T>
+__device__ __forceinline__ T e_apply(const Params<T, S> &p, const int idx[3], long long o, T eold, T se, const Tri<T> v[2],
                                      unsigned smask, double t_half)
 {
     Acc<T> acc;
@@ -424,10 +469,10 @@ __device__ __forceinline__ T e_apply(const Params<T> &p, const int idx[3], long 
                     const T mr = MUVAR ? cell_sum<C, T>(p.mu, o, p.sy, p.sz) * T(0.25) : T(1);
                     const T eta = T(p.eta0) * sqrt(mr / er);
                     // gamma = dt / (2 eta eps h_a) = (4 dt/(eps0 h_a)) / (4 eps_r) / (2 eta)
-                    gam += T(p.A[a].hi) / se / (T(2) * eta);
+                    gam += T(p.A[a].hi) * p.uA / se / (T(2) * eta);
                 } else {
                     const Link &L = p.link[f];
-                    const T *nf = static_cast<const T *>(L.F[u]);
+                    const S *nf = static_cast<const S *>(L.F[u]);
                     const int nidx = L.side < 0 ? 0 : L.n_norm + 1;  // partner H on its minus grid along a
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
@@ -442,9 +487,9 @@ __device__ __forceinline__ T e_apply(const Params<T> &p, const int idx[3], long 
     while (m) {
         const int q = __ffs(m) - 1;
         m &= m - 1;
-        const Src &S = p.src[q];
-        if (S.comp == C && (S.k < 0 || S.k == idx[2])) {
-            const double J = S.amp * waveform(S.wf, t_half, S.tw, S.t0, S.f);
+        const Src &Sr = p.src[q];
+        if (Sr.comp == C && (Sr.k < 0 || Sr.k == idx[2])) {
+            const double J = Sr.amp * waveform(Sr.wf, t_half, Sr.tw, Sr.t0, Sr.f);
             acc.add(p.AJ, T(J), T(-1));
         }
     }
@@ -454,14 +499,14 @@ __device__ __forceinline__ T e_apply(const Params<T> &p, const int idx[3], long 
 }
 
 // E half-step, general path, one component at one node (Eqs. (7)-(9), (19)-(21)).
-template <typename T, int C, bool MUVAR, bool CG = false>
-__device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long long o, T eold,
+template <typename T, int C, bool MUVAR, bool CG = false, typename S = T>
+__device__ __forceinline__ T e_node(const Params<T, S> &p, const int idx[3], long long o, T eold,
                                     unsigned smask, double t_half)
 {
     const T se = cell_sum<C, T>(p.eps, o, p.sy, p.sz);     // 4 * eps_r(node)
     Tri<T> v[2];
-    e_gather<T, C, CG>(p, idx, o, v);
-    return e_apply<T, C, MUVAR, CG>(p, idx, o, eold, se, v, smask, t_half);
+    e_gather<T, C, CG, 7>(p, idx, o, v);
+    return e_apply<T, C, MUVAR, CG, 7>(p, idx, o, eold, se, v, smask, t_half);
 }
 
 // ---------------------------------------------------------------------------
@@ -469,8 +514,8 @@ __device__ __forceinline__ T e_node(const Params<T> &p, const int idx[3], long l
 // ---------------------------------------------------------------------------
 
 // Per-thread masks of the probes / sources whose (i, j) match this column.
-template <typename T>
-__device__ __forceinline__ void column_masks(const Params<T> &p, int i, int j, bool want_h,
+template <typename T, typename S>
+__device__ __forceinline__ void column_masks(const Params<T, S> &p, int i, int j, bool want_h,
                                              unsigned long long &pm, unsigned &sm)
 {
     pm = 0ull;
@@ -484,8 +529,8 @@ __device__ __forceinline__ void column_masks(const Params<T> &p, int i, int j, b
 
 // H half-step.  ENERGY: also accumulate the leapfrog energy of Eq. (16) into
 // p.partials (FP64); STORE: write H^{n+1/2} (false = energy query only).
-template <typename T, bool ENERGY, bool STORE, bool MUVAR>
-__global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T> p)
+template <typename T, typename S, bool ENERGY, bool STORE, bool MUVAR>
+__global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T, S> p)
 {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
@@ -494,30 +539,32 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T> p)
     const int k1 = min(k0 + p.kchunk, nz + 2);
     double wacc = 0.0;
     if (i < nx + 2 && j < ny + 2) {
-        T *__restrict__ Hx = p.F[3];
-        T *__restrict__ Hy = p.F[4];
-        T *__restrict__ Hz = p.F[5];
-        const T *__restrict__ Ex = p.F[0];
-        const T *__restrict__ Ey = p.F[1];
-        const T *__restrict__ Ez = p.F[2];
+        S *__restrict__ Hx = p.F[3];
+        S *__restrict__ Hy = p.F[4];
+        S *__restrict__ Hz = p.F[5];
+        const S *__restrict__ Ex = p.F[0];
+        const S *__restrict__ Ey = p.F[1];
+        const S *__restrict__ Ez = p.F[2];
+        const double es2 = (double)p.fscale[0] * (double)p.fscale[0];   // energy of stored values
+        const double hs2 = (double)p.fscale[1] * (double)p.fscale[1];
         unsigned long long pm;
         unsigned sm;
         column_masks(p, i, j, true, pm, sm);
         const bool xyin = i >= 3 && i <= nx - 2 && j >= 3 && j <= ny - 2;
         const Coef<T> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
         long long o = (long long)k0 * p.sz + (long long)j * p.sy + i;
-        T exm = k0 > 0 ? __ldg(Ex + o - p.sz) : T(0);
-        T eym = k0 > 0 ? __ldg(Ey + o - p.sz) : T(0);
+        T exm = k0 > 0 ? ldg_s(Ex + o - p.sz) : T(0);
+        T eym = k0 > 0 ? ldg_s(Ey + o - p.sz) : T(0);
         for (int k = k0; k < k1; ++k, o += p.sz) {
-            const T exc = __ldg(Ex + o);
-            const T eyc = __ldg(Ey + o);
+            const T exc = ldg_s(Ex + o);
+            const T eyc = ldg_s(Ey + o);
             const bool fast = !ENERGY && !MUVAR && xyin && k >= 3 && k <= nz - 2 && !(pm && probe_here(p, pm, k));
             if (fast) {
-                const T ezc = __ldg(Ez + o);
-                const T ex_jm = __ldg(Ex + o - p.sy);
-                const T ey_im = __ldg(Ey + o - 1);
-                const T ez_im = __ldg(Ez + o - 1);
-                const T ez_jm = __ldg(Ez + o - p.sy);
+                const T ezc = ldg_s(Ez + o);
+                const T ex_jm = ldg_s(Ex + o - p.sy);
+                const T ey_im = ldg_s(Ey + o - 1);
+                const T ez_im = ldg_s(Ez + o - 1);
+                const T ez_jm = ldg_s(Ez + o - p.sy);
                 const T dEy_z = eyc - eym, dEz_y = ezc - ez_jm;
                 const T dEz_x = ezc - ez_im, dEx_z = exc - exm;
                 const T dEx_y = exc - ex_jm, dEy_x = eyc - ey_im;
@@ -525,61 +572,61 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T> p)
                 ax.add(Bz, dEy_z); ax.add(By, dEz_y, T(-1));
                 ay.add(Bx, dEz_x); ay.add(Bz, dEx_z, T(-1));
                 az.add(By, dEx_y); az.add(Bx, dEy_x, T(-1));
-                Hx[o] = Hx[o] + plain_increment(ax);
-                Hy[o] = Hy[o] + plain_increment(ay);
-                Hz[o] = Hz[o] + plain_increment(az);
+                st_s(Hx + o, ld_s(Hx + o) + plain_increment(ax));
+                st_s(Hy + o, ld_s(Hy + o) + plain_increment(ay));
+                st_s(Hz + o, ld_s(Hz + o) + plain_increment(az));
             } else {
                 const int idx[3] = {i, j, k};
                 // Hx (x+, y-, z-)
                 if (i <= nx && j <= ny + 1 && k <= nz + 1) {
-                    const T ho = Hx[o];
-                    const T hn = h_node<T, 3, MUVAR>(p, idx, o, ho);
-                    if (STORE) Hx[o] = hn;
+                    const T ho = ld_s(Hx + o);
+                    const T hn = quant<S>(h_node<T, 3, MUVAR>(p, idx, o, ho));
+                    if (STORE) st_s(Hx + o, hn);
                     if (STORE && pm) write_probes(p, pm, 3, k, hn);
                     if (ENERGY) {
                         const double w = norm_weight(true, i, nx) * norm_weight(false, j, ny) * norm_weight(false, k, nz);
                         const double mr = MUVAR ? 0.5 * cell_sum<3, double>(p.mu, o, p.sy, p.sz) : 1.0;
-                        wacc += p.mu0 * mr * w * (double)ho * (double)hn;
+                        wacc += p.mu0 * mr * w * (double)ho * (double)hn * hs2;
                     }
                 }
                 // Hy (x-, y+, z-)
                 if (i <= nx + 1 && j <= ny && k <= nz + 1) {
-                    const T ho = Hy[o];
-                    const T hn = h_node<T, 4, MUVAR>(p, idx, o, ho);
-                    if (STORE) Hy[o] = hn;
+                    const T ho = ld_s(Hy + o);
+                    const T hn = quant<S>(h_node<T, 4, MUVAR>(p, idx, o, ho));
+                    if (STORE) st_s(Hy + o, hn);
                     if (STORE && pm) write_probes(p, pm, 4, k, hn);
                     if (ENERGY) {
                         const double w = norm_weight(false, i, nx) * norm_weight(true, j, ny) * norm_weight(false, k, nz);
                         const double mr = MUVAR ? 0.5 * cell_sum<4, double>(p.mu, o, p.sy, p.sz) : 1.0;
-                        wacc += p.mu0 * mr * w * (double)ho * (double)hn;
+                        wacc += p.mu0 * mr * w * (double)ho * (double)hn * hs2;
                     }
                 }
                 // Hz (x-, y-, z+)
                 if (i <= nx + 1 && j <= ny + 1 && k <= nz) {
-                    const T ho = Hz[o];
-                    const T hn = h_node<T, 5, MUVAR>(p, idx, o, ho);
-                    if (STORE) Hz[o] = hn;
+                    const T ho = ld_s(Hz + o);
+                    const T hn = quant<S>(h_node<T, 5, MUVAR>(p, idx, o, ho));
+                    if (STORE) st_s(Hz + o, hn);
                     if (STORE && pm) write_probes(p, pm, 5, k, hn);
                     if (ENERGY) {
                         const double w = norm_weight(false, i, nx) * norm_weight(false, j, ny) * norm_weight(true, k, nz);
                         const double mr = MUVAR ? 0.5 * cell_sum<5, double>(p.mu, o, p.sy, p.sz) : 1.0;
-                        wacc += p.mu0 * mr * w * (double)ho * (double)hn;
+                        wacc += p.mu0 * mr * w * (double)ho * (double)hn * hs2;
                     }
                 }
                 if (ENERGY) {
                     // E^n part: eps P''' E^2 at this node position for every E component present
                     if (i <= nx + 1 && j <= ny && k <= nz) {   // Ex (x-, y+, z+)
                         const double w = norm_weight(false, i, nx) * norm_weight(true, j, ny) * norm_weight(true, k, nz);
-                        wacc += p.eps0 * 0.25 * cell_sum<0, double>(p.eps, o, p.sy, p.sz) * w * (double)exc * (double)exc;
+                        wacc += p.eps0 * 0.25 * cell_sum<0, double>(p.eps, o, p.sy, p.sz) * w * (double)exc * (double)exc * es2;
                     }
                     if (i <= nx && j <= ny + 1 && k <= nz) {   // Ey (x+, y-, z+)
                         const double w = norm_weight(true, i, nx) * norm_weight(false, j, ny) * norm_weight(true, k, nz);
-                        wacc += p.eps0 * 0.25 * cell_sum<1, double>(p.eps, o, p.sy, p.sz) * w * (double)eyc * (double)eyc;
+                        wacc += p.eps0 * 0.25 * cell_sum<1, double>(p.eps, o, p.sy, p.sz) * w * (double)eyc * (double)eyc * es2;
                     }
                     if (i <= nx && j <= ny && k <= nz + 1) {   // Ez (x+, y+, z-)
                         const double w = norm_weight(true, i, nx) * norm_weight(true, j, ny) * norm_weight(false, k, nz);
-                        const T ezc = __ldg(Ez + o);
-                        wacc += p.eps0 * 0.25 * cell_sum<2, double>(p.eps, o, p.sy, p.sz) * w * (double)ezc * (double)ezc;
+                        const T ezc = ldg_s(Ez + o);
+                        wacc += p.eps0 * 0.25 * cell_sum<2, double>(p.eps, o, p.sy, p.sz) * w * (double)ezc * (double)ezc * es2;
                     }
                 }
             }
@@ -594,8 +641,8 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T> p)
 }
 
 // E half-step with sources (J at t^{n+1/2}) and E probes.
-template <typename T, bool MUVAR>
-__global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T> p)
+template <typename T, typename S, bool MUVAR>
+__global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T, S> p)
 {
     const int i = blockIdx.x * kBlockX + threadIdx.x;
     const int j = blockIdx.y * kBlockY + threadIdx.y;
@@ -603,12 +650,12 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T> p)
     const int k0 = blockIdx.z * p.kchunk;
     const int k1 = min(k0 + p.kchunk, nz + 2);
     if (i >= nx + 2 || j >= ny + 2) return;
-    T *__restrict__ Ex = p.F[0];
-    T *__restrict__ Ey = p.F[1];
-    T *__restrict__ Ez = p.F[2];
-    const T *__restrict__ Hx = p.F[3];
-    const T *__restrict__ Hy = p.F[4];
-    const T *__restrict__ Hz = p.F[5];
+    S *__restrict__ Ex = p.F[0];
+    S *__restrict__ Ey = p.F[1];
+    S *__restrict__ Ez = p.F[2];
+    const S *__restrict__ Hx = p.F[3];
+    const S *__restrict__ Hy = p.F[4];
+    const S *__restrict__ Hz = p.F[5];
     const float *__restrict__ eps = p.eps;
     unsigned long long pm;
     unsigned sm;
@@ -618,24 +665,24 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T> p)
     const double t_half = ((double)p.step + 0.5) * p.dt;
     long long o = (long long)k0 * p.sz + (long long)j * p.sy + i;
     // plane-k carries: Hx, Hy at (i,j,k) and eps at the four cells (i..i+1, j..j+1, k)
-    T hxc = __ldg(Hx + o), hyc = __ldg(Hy + o);
+    T hxc = ldg_s(Hx + o), hyc = ldg_s(Hy + o);
     float f00 = __ldg(eps + o), f10 = __ldg(eps + o + 1), f01 = __ldg(eps + o + p.sy), f11 = __ldg(eps + o + 1 + p.sy);
     for (int k = k0; k < k1; ++k, o += p.sz) {
         const bool fast = xyin && k >= 3 && k <= nz - 2 && !(pm && probe_here(p, pm, k)) && !(sm && source_here(p, sm, k));
         // next plane (k+1) always exists inside the padded array for k <= nz
         const bool has_next = k + 1 < nz + 2;
-        const T hxn = has_next ? __ldg(Hx + o + p.sz) : T(0);
-        const T hyn = has_next ? __ldg(Hy + o + p.sz) : T(0);
+        const T hxn = has_next ? ldg_s(Hx + o + p.sz) : T(0);
+        const T hyn = has_next ? ldg_s(Hy + o + p.sz) : T(0);
         const float e00 = has_next ? __ldg(eps + o + p.sz) : 0.f;
         const float e10 = has_next ? __ldg(eps + o + p.sz + 1) : 0.f;
         const float e01 = has_next ? __ldg(eps + o + p.sz + p.sy) : 0.f;
         const float e11 = has_next ? __ldg(eps + o + p.sz + p.sy + 1) : 0.f;
         if (fast) {
-            const T hzc = __ldg(Hz + o);
-            const T hz_jp = __ldg(Hz + o + p.sy);
-            const T hz_ip = __ldg(Hz + o + 1);
-            const T hx_jp = __ldg(Hx + o + p.sy);
-            const T hy_ip = __ldg(Hy + o + 1);
+            const T hzc = ldg_s(Hz + o);
+            const T hz_jp = ldg_s(Hz + o + p.sy);
+            const T hz_ip = ldg_s(Hz + o + 1);
+            const T hx_jp = ldg_s(Hx + o + p.sy);
+            const T hy_ip = ldg_s(Hy + o + 1);
             Acc<T> ax, ay, az;
             ax.add(Ay, hz_jp - hzc); ax.add(Az, hyn - hyc, T(-1));
             ay.add(Az, hxn - hxc);   ay.add(Ax, hz_ip - hzc, T(-1));
@@ -645,24 +692,24 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T> p)
             const T sx = (T(f00) + T(f01)) + (T(e00) + T(e01));
             const T sy = (T(f00) + T(f10)) + (T(e00) + T(e10));
             const T sz = (T(f00) + T(f10)) + (T(f01) + T(f11));
-            Ex[o] = Ex[o] + scaled_increment(ax, sx);
-            Ey[o] = Ey[o] + scaled_increment(ay, sy);
-            Ez[o] = Ez[o] + scaled_increment(az, sz);
+            st_s(Ex + o, ld_s(Ex + o) + scaled_increment(ax, sx));
+            st_s(Ey + o, ld_s(Ey + o) + scaled_increment(ay, sy));
+            st_s(Ez + o, ld_s(Ez + o) + scaled_increment(az, sz));
         } else {
             const int idx[3] = {i, j, k};
             if (i <= nx + 1 && j <= ny && k <= nz) {          // Ex (x-, y+, z+)
-                const T en = e_node<T, 0, MUVAR>(p, idx, o, Ex[o], sm, t_half);
-                Ex[o] = en;
+                const T en = quant<S>(e_node<T, 0, MUVAR>(p, idx, o, ld_s(Ex + o), sm, t_half));
+                st_s(Ex + o, en);
                 if (pm) write_probes(p, pm, 0, k, en);
             }
             if (i <= nx && j <= ny + 1 && k <= nz) {          // Ey (x+, y-, z+)
-                const T en = e_node<T, 1, MUVAR>(p, idx, o, Ey[o], sm, t_half);
-                Ey[o] = en;
+                const T en = quant<S>(e_node<T, 1, MUVAR>(p, idx, o, ld_s(Ey + o), sm, t_half));
+                st_s(Ey + o, en);
                 if (pm) write_probes(p, pm, 1, k, en);
             }
             if (i <= nx && j <= ny && k <= nz + 1) {          // Ez (x+, y+, z-)
-                const T en = e_node<T, 2, MUVAR>(p, idx, o, Ez[o], sm, t_half);
-                Ez[o] = en;
+                const T en = quant<S>(e_node<T, 2, MUVAR>(p, idx, o, ld_s(Ez + o), sm, t_half));
+                st_s(Ez + o, en);
                 if (pm) write_probes(p, pm, 2, k, en);
             }
         }
@@ -685,6 +732,33 @@ __global__ void __launch_bounds__(256) energy_finalize(const double *__restrict_
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = 0.5 * red[0];
+}
+
+// FP16 field storage: natural-extent FP32 array (e0 x e1 x e2, x fastest) in,
+// padded stored values (value / scale, rounded to nearest) out, and back.
+__global__ void put_field_h(const float *__restrict__ src, int e0, int e1, int e2, __half *__restrict__ dst,
+                            long long sy, long long sz, float inv_scale)
+{
+    const long long total = (long long)e0 * e1 * e2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % e0);
+        const int j = (int)((q / e0) % e1);
+        const int k = (int)(q / ((long long)e0 * e1));
+        dst[(long long)k * sz + (long long)j * sy + i] = __float2half_rn(src[q] * inv_scale);
+    }
+}
+__global__ void get_field_h(const __half *__restrict__ src, int e0, int e1, int e2, long long sy, long long sz,
+                            float scale, float *__restrict__ dst)
+{
+    const long long total = (long long)e0 * e1 * e2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % e0);
+        const int j = (int)((q / e0) % e1);
+        const int k = (int)(q / ((long long)e0 * e1));
+        dst[q] = __half2float(src[(long long)k * sz + (long long)j * sy + i]) * scale;
+    }
 }
 
 // Ghost-padded cell array (coefficient build, once per grid): padded (cx+1,

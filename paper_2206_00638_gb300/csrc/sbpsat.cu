@@ -52,7 +52,9 @@ struct sbp_sim {
     int flags = 0;
     int device = 0;
     cudaStream_t stream = nullptr;
-    size_t esize = 4;
+    size_t esize = 4;                     // bytes per stored field element
+    size_t psize = 4;                     // bytes per probe sample (the arithmetic type)
+    double fscale[2] = {1.0, 1.0};        // physical value = stored value * fscale[E / H] (FP16 storage)
     long long sy = 0, sz = 0;
     size_t field_elems = 0;               // elements per padded array, slack included
     void *set[2][6] = {{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr},
@@ -111,7 +113,9 @@ bool desc_valid(const sbp_grid_desc *d)
     if (!(d->dx > 0) || !(d->dy > 0) || !(d->dz > 0)) return false;
     if (!(d->cfl_fraction > 0)) return false;
     if (d->cfl_fraction > 1.0 && !(d->flags & SBP_FLAG_ALLOW_UNSTABLE)) return false;
-    if (d->precision != SBP_FP32 && d->precision != SBP_FP64) return false;
+    if (d->precision != SBP_FP32 && d->precision != SBP_FP64 && d->precision != SBP_FP32_FP16STORE) return false;
+    for (int q = 0; q < 2; q++)
+        if (!(d->field_scale[q] >= 0.0) || !std::isfinite(d->field_scale[q])) return false;
     for (int f = 0; f < 6; f++)
         if (d->face[f] < SBP_PEC || d->face[f] > SBP_INTERFACE) return false;
     if (d->energy_every < 0) return false;
@@ -128,7 +132,7 @@ bool desc_valid(const sbp_grid_desc *d)
 Layout make_layout(const sbp_grid_desc *d)
 {
     Layout L;
-    L.esize = d->precision == SBP_FP64 ? 8 : 4;
+    L.esize = d->precision == SBP_FP64 ? 8 : d->precision == SBP_FP32_FP16STORE ? 2 : 4;
     L.sy = (long long)round_up((size_t)d->nx + 2, 8);
     L.sz = L.sy * (d->ny + 2);
     L.field_elems = (size_t)L.sz * (d->nz + 3);          // nz+2 planes + one slack plane
@@ -149,7 +153,7 @@ Layout make_layout(const sbp_grid_desc *d)
     L.grid = dim3(gx, gy, gz);
     L.npartials = (long long)gx * gy * gz;
     L.partial_bytes = round_up((size_t)L.npartials * sizeof(double), 256);
-    L.fused = d->precision == SBP_FP32 && !d->mu_r && d->nx >= 8 && d->ny >= 8 && d->nz >= 8 &&
+    L.fused = d->precision != SBP_FP64 && !d->mu_r && d->nx >= 8 && d->ny >= 8 && d->nz >= 8 &&
               !std::getenv("SBP_NO_FUSED");
     if (L.fused) {
         const int tx = (d->nx - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
@@ -205,16 +209,18 @@ EncodeTiledFn encode_fn()
     return fn;
 }
 
-// 3D map over a padded FP32 array: dims (pitch, ny+2, nz+2), box (kFBX, rows, 1).
-int encode_one(CUtensorMap *m, void *base, const sbp_sim *s, int rows)
+// 3D map over a padded array of 4-byte (FP32) or 2-byte (FP16) elements:
+// dims (pitch, ny+2, nz+2), box (bx, rows, 1).
+int encode_one(CUtensorMap *m, void *base, const sbp_sim *s, int rows, int esize, int bx)
 {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return SBP_ECUDA;
     const cuuint64_t dims[3] = {(cuuint64_t)s->sy, (cuuint64_t)(s->n[1] + 2), (cuuint64_t)(s->n[2] + 2)};
-    const cuuint64_t strides[2] = {(cuuint64_t)s->sy * 4, (cuuint64_t)s->sz * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)sbp::kFBX, (cuuint32_t)rows, 1};
+    const cuuint64_t strides[2] = {(cuuint64_t)s->sy * esize, (cuuint64_t)s->sz * esize};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    const CUtensorMapDataType dt = esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    CUresult r = fn(m, dt, 3, base, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? SBP_OK : SBP_ECUDA;
@@ -222,14 +228,16 @@ int encode_one(CUtensorMap *m, void *base, const sbp_sim *s, int rows)
 
 int encode_maps(sbp_sim *s)
 {
+    const int es = (int)s->esize;
+    const int bx = es == 2 ? sbp::FusedGeom<__half>::kBX : sbp::FusedGeom<float>::kBX;
     for (int set = 0; set < 2; set++) {
         for (int f = 0; f < 3; f++) {
-            int rc = encode_one(&s->maps[set].e[f], s->set[set][f], s, sbp::kERows);
+            int rc = encode_one(&s->maps[set].e[f], s->set[set][f], s, sbp::kERows, es, bx);
             if (rc) return rc;
-            rc = encode_one(&s->maps[set].h[f], s->set[set][3 + f], s, sbp::kHRows);
+            rc = encode_one(&s->maps[set].h[f], s->set[set][3 + f], s, sbp::kHRows, es, bx);
             if (rc) return rc;
         }
-        int rc = encode_one(&s->maps[set].eps, s->eps, s, sbp::kHRows);
+        int rc = encode_one(&s->maps[set].eps, s->eps, s, sbp::kHRows, 4, bx);
         if (rc) return rc;
     }
     return SBP_OK;
@@ -245,6 +253,13 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     s->energy_every = d->energy_every;
     s->flags = d->flags;
     s->esize = L.esize;
+    s->psize = d->precision == SBP_FP64 ? 8 : 4;
+    if (d->precision == SBP_FP32_FP16STORE) {
+        // default scales: E in V/m as is, H as eta0 * H (the two then have
+        // comparable magnitudes in a wave)
+        s->fscale[0] = d->field_scale[0] > 0 ? d->field_scale[0] : 1.0;
+        s->fscale[1] = d->field_scale[1] > 0 ? d->field_scale[1] : 1.0 / std::sqrt(kMu0 / kEps0);
+    }
     s->sy = L.sy; s->sz = L.sz;
     s->field_elems = L.field_elems;
     s->kchunk = L.kchunk;
@@ -338,12 +353,12 @@ sbp::Coef<T> split(double v)
 // Kernel parameters reading E from field set eset and H from set hset.
 // Interface partners: E from the partner's current set; H from the set the
 // partner's H^{n+1/2} lands in this step (its new set when it runs fused).
-template <typename T>
-int make_params(const sbp_sim *s, sbp::Params<T> &p, int eset, int hset)
+template <typename T, typename S = T>
+int make_params(const sbp_sim *s, sbp::Params<T, S> &p, int eset, int hset)
 {
     std::memset(&p, 0, sizeof(p));
-    for (int c = 0; c < 3; c++) p.F[c] = static_cast<T *>(s->set[eset][c]);
-    for (int c = 3; c < 6; c++) p.F[c] = static_cast<T *>(s->set[hset][c]);
+    for (int c = 0; c < 3; c++) p.F[c] = static_cast<S *>(s->set[eset][c]);
+    for (int c = 3; c < 6; c++) p.F[c] = static_cast<S *>(s->set[hset][c]);
     p.eps = s->eps;
     p.mu = s->mu;
     for (int a = 0; a < 3; a++) p.n[a] = s->n[a];
@@ -363,13 +378,20 @@ int make_params(const sbp_sim *s, sbp::Params<T> &p, int eset, int hset)
             p.link[f].side = (s->nbr_face[f] % 2) ? 1 : -1;
         }
     }
+    // stored fields are E / sE and H / sH: the H update takes B sE / sH, the
+    // E update A sH / sE and the source term AJ / sE (all 1 unless FP16 storage)
     const double bscale = s->mu ? 2.0 : 1.0;
+    const double sE = s->fscale[0], sH = s->fscale[1];
     for (int a = 0; a < 3; a++) {
-        p.B[a] = split<T>(bscale * s->dt / (kMu0 * s->h[a]));
-        p.A[a] = split<T>(4.0 * s->dt / (kEps0 * s->h[a]));
+        p.B[a] = split<T>(bscale * s->dt / (kMu0 * s->h[a]) * (sE / sH));
+        p.A[a] = split<T>(4.0 * s->dt / (kEps0 * s->h[a]) * (sH / sE));
         p.h[a] = s->h[a];
     }
-    p.AJ = split<T>(4.0 * s->dt / kEps0);
+    p.AJ = split<T>(4.0 * s->dt / kEps0 / sE);
+    p.fscale[0] = (T)sE;
+    p.fscale[1] = (T)sH;
+    p.uB = (T)(sH / sE);
+    p.uA = (T)(sE / sH);
     p.dt = s->dt;
     p.eta0 = std::sqrt(kMu0 / kEps0);
     p.eps0 = kEps0;
@@ -378,7 +400,7 @@ int make_params(const sbp_sim *s, sbp::Params<T> &p, int eset, int hset)
     for (int q = 0; q < p.nsrc; q++) p.src[q] = s->src[q];
     p.nprb = (int)s->prb.size();
     for (int q = 0; q < p.nprb; q++) p.prb[q] = s->prb[q];
-    p.probe_buf = static_cast<T *>(s->probe_buf);
+    p.probe_buf = static_cast<T *>(s->probe_buf);   // samples in the arithmetic type
     p.probe_cap = s->probe_buf ? s->probe_cap : 0;
     p.probe_slot = s->step - s->probe_base;
     p.step = s->step;
@@ -387,60 +409,66 @@ int make_params(const sbp_sim *s, sbp::Params<T> &p, int eset, int hset)
     return SBP_OK;
 }
 
-template <typename T>
+template <typename T, typename S>
 int launch_h(const sbp_sim *s, bool energy, bool store)
 {
-    sbp::Params<T> p;
-    int rc = make_params<T>(s, p, s->cur, s->cur);
+    sbp::Params<T, S> p;
+    int rc = make_params<T, S>(s, p, s->cur, s->cur);
     if (rc) return rc;
     const dim3 block(sbp::kBlockX, sbp::kBlockY);
     const bool muv = s->mu != nullptr;
     if (!energy) {
-        if (muv) sbp::h_update<T, false, true, true><<<s->grid, block, 0, s->stream>>>(p);
-        else sbp::h_update<T, false, true, false><<<s->grid, block, 0, s->stream>>>(p);
+        if (muv) sbp::h_update<T, S, false, true, true><<<s->grid, block, 0, s->stream>>>(p);
+        else sbp::h_update<T, S, false, true, false><<<s->grid, block, 0, s->stream>>>(p);
     } else if (store) {
-        if (muv) sbp::h_update<T, true, true, true><<<s->grid, block, 0, s->stream>>>(p);
-        else sbp::h_update<T, true, true, false><<<s->grid, block, 0, s->stream>>>(p);
+        if (muv) sbp::h_update<T, S, true, true, true><<<s->grid, block, 0, s->stream>>>(p);
+        else sbp::h_update<T, S, true, true, false><<<s->grid, block, 0, s->stream>>>(p);
     } else {
-        if (muv) sbp::h_update<T, true, false, true><<<s->grid, block, 0, s->stream>>>(p);
-        else sbp::h_update<T, true, false, false><<<s->grid, block, 0, s->stream>>>(p);
+        if (muv) sbp::h_update<T, S, true, false, true><<<s->grid, block, 0, s->stream>>>(p);
+        else sbp::h_update<T, S, true, false, false><<<s->grid, block, 0, s->stream>>>(p);
     }
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
 }
 
-template <typename T>
+template <typename T, typename S>
 int launch_e(const sbp_sim *s)
 {
-    sbp::Params<T> p;
-    int rc = make_params<T>(s, p, s->cur, s->cur);
+    sbp::Params<T, S> p;
+    int rc = make_params<T, S>(s, p, s->cur, s->cur);
     if (rc) return rc;
     const dim3 block(sbp::kBlockX, sbp::kBlockY);
-    if (s->mu) sbp::e_update<T, true><<<s->grid, block, 0, s->stream>>>(p);
-    else sbp::e_update<T, false><<<s->grid, block, 0, s->stream>>>(p);
+    if (s->mu) sbp::e_update<T, S, true><<<s->grid, block, 0, s->stream>>>(p);
+    else sbp::e_update<T, S, false><<<s->grid, block, 0, s->stream>>>(p);
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
 }
 
 int launch_h_any(const sbp_sim *s, bool energy, bool store)
 {
-    return s->prec == SBP_FP64 ? launch_h<double>(s, energy, store) : launch_h<float>(s, energy, store);
+    if (s->prec == SBP_FP64) return launch_h<double, double>(s, energy, store);
+    if (s->prec == SBP_FP32_FP16STORE) return launch_h<float, __half>(s, energy, store);
+    return launch_h<float, float>(s, energy, store);
 }
 int launch_e_any(const sbp_sim *s)
 {
-    return s->prec == SBP_FP64 ? launch_e<double>(s) : launch_e<float>(s);
+    if (s->prec == SBP_FP64) return launch_e<double, double>(s);
+    if (s->prec == SBP_FP32_FP16STORE) return launch_e<float, __half>(s);
+    return launch_e<float, float>(s);
 }
 
-// The one-pass interior step (old set -> new set).
 // Parameters of the one-pass interior step reading set `old`, writing set old^1.
-int make_fused_params(const sbp_sim *s, int old, sbp::FusedParams &fp)
+template <typename S>
+int make_fused_params(const sbp_sim *s, int old, sbp::FusedParamsT<S> &fp)
 {
-    sbp::Params<float> p;
-    int rc = make_params<float>(s, p, old, old);
+    sbp::Params<float, S> p;
+    int rc = make_params<float, S>(s, p, old, old);
     if (rc) return rc;
-    float **ns = reinterpret_cast<float **>(const_cast<void **>(s->set[old ^ 1]));
+    S **ns = reinterpret_cast<S **>(const_cast<void **>(s->set[old ^ 1]));
     std::memset(&fp, 0, sizeof(fp));
     for (int c = 0; c < 6; c++) fp.out[c] = ns[c];
+    fp.pscale[0] = p.fscale[0];
+    fp.pscale[1] = p.fscale[1];
     for (int a = 0; a < 3; a++) { fp.n[a] = s->n[a]; fp.B[a] = p.B[a]; fp.A[a] = p.A[a]; }
     fp.sy = s->sy;
     fp.sz = s->sz;
@@ -465,43 +493,78 @@ int set_fused_smem_attr()
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !done[dev]) {
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, sbp::kFusedSmem));
+        const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, float>, attr, sbp::kFusedSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float>, attr, sbp::kFusedSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half>, attr, sbp::kFusedSmemH));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half>, attr, sbp::kFusedSmemH));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched, attr, sbp::kFusedSmem));
         done[dev] = true;
     }
     return SBP_OK;
 }
 
 // The one-pass interior step (old set -> new set).
-int launch_fused_interior_only(sbp_sim *s)
+template <typename S>
+int launch_fused_interior_t(sbp_sim *s)
 {
     const int old = s->cur;
-    sbp::FusedParams fp;
-    int rc = make_fused_params(s, old, fp);
+    sbp::FusedParamsT<S> fp;
+    int rc = make_fused_params<S>(s, old, fp);
     if (rc) return rc;
     rc = set_fused_smem_attr();
     if (rc) return rc;
+    constexpr int smem = sbp::FusedGeom<S>::kSmem;
     if (fp.nsrc > 0)
-        sbp::fused_interior<true><<<s->fused_grid, sbp::kFTY * 32, sbp::kFusedSmem, s->stream>>>(s->maps[old], fp);
+        sbp::fused_interior<true, S><<<s->fused_grid, sbp::kFTY * 32, smem, s->stream>>>(s->maps[old], fp);
     else
-        sbp::fused_interior<false><<<s->fused_grid, sbp::kFTY * 32, sbp::kFusedSmem, s->stream>>>(s->maps[old], fp);
+        sbp::fused_interior<false, S><<<s->fused_grid, sbp::kFTY * 32, smem, s->stream>>>(s->maps[old], fp);
+    SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+// Band H (old -> new) on stream st.
+template <typename S>
+int launch_band_h_t(sbp_sim *s, cudaStream_t st)
+{
+    const int old = s->cur, nw = s->cur ^ 1;
+    sbp::Params<float, S> p;
+    int rc = make_params<float, S>(s, p, old, old);
+    if (rc) return rc;
+    const sbp::Band &bh = s->band_hb;
+    S **ns = reinterpret_cast<S **>(s->set[nw]);
+    sbp::band_h<float, false><<<bh.ctas, 256, 0, st>>>(p, bh, ns[3], ns[4], ns[5]);
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
 }
 
 // Band E from E^n (old) and H^{n+1/2} (new) into the new set, on stream st.
-int launch_band_e(sbp_sim *s, cudaStream_t st)
+template <typename S>
+int launch_band_e_t(sbp_sim *s, cudaStream_t st)
 {
     const int old = s->cur, nw = s->cur ^ 1;
-    sbp::Params<float> p;
-    int rc = make_params<float>(s, p, old, nw);
+    sbp::Params<float, S> p;
+    int rc = make_params<float, S>(s, p, old, nw);
     if (rc) return rc;
     const sbp::Band &be = s->band_eb;
-    float **ns = reinterpret_cast<float **>(s->set[nw]);
+    S **ns = reinterpret_cast<S **>(s->set[nw]);
     sbp::band_e<float, false><<<be.ctas, 256, 0, st>>>(p, be, ns[0], ns[1], ns[2]);
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
+}
+
+// The fused path runs for FP32 arithmetic with FP32 or FP16 storage.
+int launch_fused_interior_only(sbp_sim *s)
+{
+    return s->prec == SBP_FP32_FP16STORE ? launch_fused_interior_t<__half>(s) : launch_fused_interior_t<float>(s);
+}
+int launch_band_h(sbp_sim *s, cudaStream_t st)
+{
+    return s->prec == SBP_FP32_FP16STORE ? launch_band_h_t<__half>(s, st) : launch_band_h_t<float>(s, st);
+}
+int launch_band_e(sbp_sim *s, cudaStream_t st)
+{
+    return s->prec == SBP_FP32_FP16STORE ? launch_band_e_t<__half>(s, st) : launch_band_e_t<float>(s, st);
 }
 
 // Fused path, phase 1: the one-pass interior step on the main stream and,
@@ -510,18 +573,11 @@ int launch_band_e(sbp_sim *s, cudaStream_t st)
 // for that partner's band H instead: phase 2).  Joined before returning.
 int launch_fused_phase1(sbp_sim *s, bool chain_e)
 {
-    const int old = s->cur, nw = s->cur ^ 1;
-    sbp::Params<float> p;
-    int rc = make_params<float>(s, p, old, old);
-    if (rc) return rc;
-    const sbp::Band &bh = s->band_hb;
-    float **ns = reinterpret_cast<float **>(s->set[nw]);
     SBP_CUDA(cudaEventRecord(s->ev_fork, s->stream));
-    rc = launch_fused_interior_only(s);
+    int rc = launch_fused_interior_only(s);
     if (rc) return rc;
     SBP_CUDA(cudaStreamWaitEvent(s->side, s->ev_fork, 0));
-    sbp::band_h<float, false><<<bh.ctas, 256, 0, s->side>>>(p, bh, ns[3], ns[4], ns[5]);
-    SBP_CUDA(cudaGetLastError());
+    if ((rc = launch_band_h(s, s->side))) return rc;
     if (chain_e && (rc = launch_band_e(s, s->side))) return rc;
     SBP_CUDA(cudaEventRecord(s->ev_join, s->side));
     SBP_CUDA(cudaStreamWaitEvent(s->stream, s->ev_join, 0));
@@ -572,16 +628,16 @@ int noalloc_scratch(int device, double **out)
 
 // The energy query of sbp_energy with the partial sums in `partials` and the
 // result written to the device pointer `dst`.
-template <typename T>
+template <typename T, typename S>
 int energy_into_t(const sbp_sim *s, double *partials, double *dst)
 {
-    sbp::Params<T> p;
-    int rc = make_params<T>(s, p, s->cur, s->cur);
+    sbp::Params<T, S> p;
+    int rc = make_params<T, S>(s, p, s->cur, s->cur);
     if (rc) return rc;
     p.partials = partials;
     const dim3 block(sbp::kBlockX, sbp::kBlockY);
-    if (s->mu) sbp::h_update<T, true, false, true><<<s->grid, block, 0, s->stream>>>(p);
-    else sbp::h_update<T, true, false, false><<<s->grid, block, 0, s->stream>>>(p);
+    if (s->mu) sbp::h_update<T, S, true, false, true><<<s->grid, block, 0, s->stream>>>(p);
+    else sbp::h_update<T, S, true, false, false><<<s->grid, block, 0, s->stream>>>(p);
     SBP_CUDA(cudaGetLastError());
     sbp::energy_finalize<<<1, 256, 0, s->stream>>>(partials, s->npartials, dst);
     SBP_CUDA(cudaGetLastError());
@@ -590,7 +646,9 @@ int energy_into_t(const sbp_sim *s, double *partials, double *dst)
 
 int energy_into(const sbp_sim *s, double *partials, double *dst)
 {
-    return s->prec == SBP_FP64 ? energy_into_t<double>(s, partials, dst) : energy_into_t<float>(s, partials, dst);
+    if (s->prec == SBP_FP64) return energy_into_t<double, double>(s, partials, dst);
+    if (s->prec == SBP_FP32_FP16STORE) return energy_into_t<float, __half>(s, partials, dst);
+    return energy_into_t<float, float>(s, partials, dst);
 }
 
 int ensure_series(sbp_sim *s, long long need)
@@ -752,16 +810,11 @@ int step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, in
                         s->face[2] != SBP_INTERFACE && s->face[3] != SBP_INTERFACE && s->face[4] != SBP_INTERFACE &&
                         s->face[5] != SBP_INTERFACE;
         if (s->fused_step) {
-            // phase 1 = band_h + fused_interior, launched separately to time each
-            const int old = s->cur, nw = s->cur ^ 1;
-            sbp::Params<float> p;
-            if ((rc = make_params<float>(s, p, old, old))) break;
-            const sbp::Band &bh = s->band_hb;
-            float **ns = reinterpret_cast<float **>(s->set[nw]);
+            // the three kernels of a fused step, one after another on the
+            // stream so that each is timed alone
             if ((rc = mark(2))) break;
-            sbp::band_h<float, false><<<bh.ctas, 256, 0, s->stream>>>(p, bh, ns[3], ns[4], ns[5]);
+            if ((rc = launch_band_h(s, s->stream))) break;
             if ((rc = mark(-1))) break;
-            // fused_interior alone: reuse phase 1 with the band launch skipped
             if ((rc = mark(3))) break;
             if ((rc = launch_fused_interior_only(s))) break;
             if ((rc = mark(-1))) break;
@@ -972,6 +1025,7 @@ int sbp_connect(sbp_sim *a, int fa, sbp_sim *b, int fb)
         if (a->n[t] != b->n[t] || a->h[t] != b->h[t]) return SBP_ENOTCONFORMING;
     }
     if (a->dt != b->dt) return SBP_ENOTCONFORMING;
+    if (a->fscale[0] != b->fscale[0] || a->fscale[1] != b->fscale[1]) return SBP_EINVAL;
     a->face[fa] = SBP_INTERFACE; a->nbr[fa] = b; a->nbr_face[fa] = fb;
     b->face[fb] = SBP_INTERFACE; b->nbr[fb] = a; b->nbr_face[fb] = fa;
     return SBP_OK;
@@ -982,6 +1036,23 @@ int sbp_set_field(sbp_sim *s, int comp, const void *src, int is_device)
     int e[3];
     if (!s || !src || extents_of(s, comp, e)) return SBP_EINVAL;
     cudaSetDevice(s->device);
+    if (s->prec == SBP_FP32_FP16STORE) {
+        // FP32 values in; stored as value / scale in FP16
+        const size_t bytes = (size_t)e[0] * e[1] * e[2] * sizeof(float);
+        const float *d_src = static_cast<const float *>(src);
+        float *tmp = nullptr;
+        if (!is_device) {
+            SBP_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&tmp), bytes, s->stream));
+            SBP_CUDA(cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, s->stream));
+            d_src = tmp;
+        }
+        sbp::put_field_h<<<1024, 256, 0, s->stream>>>(d_src, e[0], e[1], e[2], static_cast<__half *>(s->set[s->cur][comp]),
+                                                       s->sy, s->sz, (float)(1.0 / s->fscale[comp >= 3]));
+        SBP_CUDA(cudaGetLastError());
+        if (tmp) SBP_CUDA(cudaFreeAsync(tmp, s->stream));
+        if (!is_device) SBP_CUDA(cudaStreamSynchronize(s->stream));
+        return SBP_OK;
+    }
     cudaMemcpy3DParms m = {};
     m.srcPtr = make_cudaPitchedPtr(const_cast<void *>(src), e[0] * s->esize, e[0] * s->esize, e[1]);
     m.dstPtr = make_cudaPitchedPtr(s->set[s->cur][comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
@@ -997,6 +1068,22 @@ int sbp_get_field(sbp_sim *s, int comp, void *dst, int to_device)
     int e[3];
     if (!s || !dst || extents_of(s, comp, e)) return SBP_EINVAL;
     cudaSetDevice(s->device);
+    if (s->prec == SBP_FP32_FP16STORE) {
+        // stored FP16 values times the field's scale, out as FP32
+        const size_t bytes = (size_t)e[0] * e[1] * e[2] * sizeof(float);
+        float *d_dst = static_cast<float *>(dst);
+        if (!to_device) SBP_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&d_dst), bytes, s->stream));
+        sbp::get_field_h<<<1024, 256, 0, s->stream>>>(static_cast<const __half *>(s->set[s->cur][comp]), e[0], e[1], e[2],
+                                                       s->sy, s->sz, (float)s->fscale[comp >= 3], d_dst);
+        SBP_CUDA(cudaGetLastError());
+        if (!to_device) {
+            SBP_CUDA(cudaMemcpyAsync(dst, d_dst, bytes, cudaMemcpyDeviceToHost, s->stream));
+            SBP_CUDA(cudaFreeAsync(d_dst, s->stream));
+            SBP_CUDA(cudaStreamSynchronize(s->stream));
+            return check_error_flag(s);
+        }
+        return SBP_OK;
+    }
     cudaMemcpy3DParms m = {};
     m.srcPtr = make_cudaPitchedPtr(s->set[s->cur][comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
     m.dstPtr = make_cudaPitchedPtr(dst, e[0] * s->esize, e[0] * s->esize, e[1]);
@@ -1051,8 +1138,8 @@ int sbp_reserve_probes(sbp_sim *s, int64_t nsteps)
     s->probe_cap = 0;
     const size_t np = std::max<size_t>(1, s->prb.size());
     if (nsteps > 0) {
-        SBP_CUDA(cudaMalloc(&s->probe_buf, np * nsteps * s->esize));
-        SBP_CUDA(cudaMemsetAsync(s->probe_buf, 0, np * nsteps * s->esize, s->stream));
+        SBP_CUDA(cudaMalloc(&s->probe_buf, np * nsteps * s->psize));
+        SBP_CUDA(cudaMemsetAsync(s->probe_buf, 0, np * nsteps * s->psize, s->stream));
         s->probe_cap = nsteps;
     }
     s->probe_base = s->step;
@@ -1105,13 +1192,13 @@ int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples)
     if (nsamples) *nsamples = rec;
     const size_t np = s->prb.size();
     if (np == 0 || !s->probe_buf || cap == 0) return SBP_OK;
-    std::vector<char> host(np * s->probe_cap * s->esize);
+    std::vector<char> host(np * s->probe_cap * s->psize);
     SBP_CUDA(cudaMemcpy(host.data(), s->probe_buf, host.size(), cudaMemcpyDeviceToHost));
     const long long m = std::min<long long>(cap, s->probe_cap);
     for (size_t q = 0; q < np; q++)
         for (long long t = 0; t < m; t++) {
             const size_t src = q * s->probe_cap + t;
-            out[q * cap + t] = s->esize == 8 ? reinterpret_cast<double *>(host.data())[src]
+            out[q * cap + t] = s->psize == 8 ? reinterpret_cast<double *>(host.data())[src]
                                              : (double)reinterpret_cast<float *>(host.data())[src];
         }
     return SBP_OK;
@@ -1234,7 +1321,8 @@ int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
 int sbp_batch_add(sbp_batch *b, sbp_sim *s, int64_t nsteps)
 {
     if (!b || !s || nsteps < 0) return SBP_EINVAL;
-    if (!s->fused_ok || s->stream != b->stream || s->energy_every > 0 || s->device != b->device) return SBP_EINVAL;
+    if (!s->fused_ok || s->prec != SBP_FP32 || s->stream != b->stream || s->energy_every > 0 || s->device != b->device)
+        return SBP_EINVAL;
     for (int f = 0; f < 6; f++)
         if (s->face[f] == SBP_INTERFACE) return SBP_EINVAL;
     for (auto &m : b->m)

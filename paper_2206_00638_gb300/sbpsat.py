@@ -77,6 +77,7 @@ class GridDesc(C.Structure):
         ("precision", C.c_int32),
         ("energy_every", C.c_int32),
         ("flags", C.c_int32),
+        ("field_scale", C.c_double * 2),
     ]
 
 
@@ -176,7 +177,7 @@ class Sim:
     """
 
     def __init__(self, n, h, faces, eps_r=None, mu_r=None, cfl=0.95, precision=FP32,
-                 energy_every=0, flags=0, stream=None, torch_memory=True):
+                 energy_every=0, flags=0, stream=None, torch_memory=True, field_scale=(0.0, 0.0)):
         L = lib()
         self.n = tuple(int(v) for v in n)
         self.h = tuple(float(v) for v in h)
@@ -202,6 +203,7 @@ class Sim:
         d.precision = int(precision)
         d.energy_every = int(energy_every)
         d.flags = int(flags)
+        d.field_scale[0], d.field_scale[1] = float(field_scale[0]), float(field_scale[1])
         self._desc = d
         self.stream = _stream_ptr(stream)
         h_out = C.c_void_p()
@@ -359,12 +361,13 @@ def energy_group(sims):
     return w.value
 
 
-def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_every=0):
-    """Create the GPU blocks of a workloads.Workload (fields, sources, probes, links)."""
+def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_every=0, field_scale=(0.0, 0.0)):
+    """Create the GPU blocks of a workloads.Workload (fields, sources, probes, links).
+    field_scale: (E, H) scales of FP16 storage (0 = library default)."""
     sims = []
     for b in w.blocks:
         s = Sim(b.n, b.h, b.faces, eps_r=b.eps_r, mu_r=b.mu_r, cfl=w.cfl, precision=precision,
-                stream=stream, torch_memory=torch_memory, energy_every=energy_every)
+                stream=stream, torch_memory=torch_memory, energy_every=energy_every, field_scale=field_scale)
         if b.fields is not None:
             for c in range(6):
                 s.set_field(c, b.fields[c])

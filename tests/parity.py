@@ -74,19 +74,30 @@ def component_errors(sims, blocks):
 
 
 def probe_error(sims, blocks):
-    """Max probe error, each probe scaled by the peak of all probes of its field (E or H)."""
-    worst = 0.0
+    """Max probe error, each probe scaled by the peak of all probes of its field (E or H)
+    over every block (a probe the wave has not reached yet is measured against the
+    field's peak elsewhere, not against its own near-zero values)."""
+    pairs = []
     for s, b in zip(sims, blocks):
         if b.nprobes == 0:
             continue
         g, r = s.probes(), b.probes()[:, : s.probes().shape[1]]
         comps = np.array([p.comp for p in b.probe_specs]) if hasattr(b, "probe_specs") else None
+        pairs.append((g, r, comps))
+    if not pairs:
+        return 0.0
+    fpeak = {}
+    for isH in (False, True):
+        vals = [np.abs(r[(c >= 3) == isH]).max() for g, r, c in pairs if c is not None and ((c >= 3) == isH).any()]
+        fpeak[isH] = max(vals) if vals else 0.0
+    worst = 0.0
+    for g, r, comps in pairs:
         peak = np.max(np.abs(r), axis=1)
         if comps is not None:
             for isH in (False, True):
                 sel = (comps >= 3) == isH
                 if sel.any():
-                    peak[sel] = max(peak[sel].max(), 1e-300)
+                    peak[sel] = max(fpeak[isH], 1e-300)
         peak[peak == 0] = 1.0
         worst = max(worst, float(np.max(np.abs(g - r) / peak[:, None])))
     return worst

@@ -212,3 +212,14 @@ def test_fused_path_with_energy_monitor_steps():
     blocks = parity.oracle_run(w, 90, sims[0].dt)
     errs = parity.compare(sims, blocks)
     assert max(errs[0]) < TOL[sbpsat.FP32], errs
+
+
+def test_two_block_full_size_200_steps():
+    """Two-block interface workload at its full size (two 192x192x96 blocks joined on z,
+    absorbing outer faces, eps_r patches, Ex sheet source): every field of both blocks
+    after the first 200 steps, FP32, in the group stepping the benchmark would use."""
+    w = wl.two_block(steps=200)
+    errs, perr = _run_and_compare(w, 200, sbpsat.FP32)
+    for e in errs:
+        assert max(e) < 1e-5, errs
+    assert perr < 1e-4
