@@ -54,6 +54,7 @@ def parse():
                     help="fp16: FP32 arithmetic with FP16 field storage")
     ap.add_argument("--requests", type=int, default=512, help="serving workload: number of requests")
     ap.add_argument("--rho", type=float, default=0.9, help="serving workload: offered load / plain throughput")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default z-block depth")
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--budget-gib", type=float, default=8.0)
     return ap.parse_args()
@@ -176,6 +177,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sim = sbpsat.from_workload(w, stream=stream, precision=prec)[0]
     sim.reserve_probes(args.warmup + args.steps + min(args.steps, 400) + 8)
+    depth = None
+    if not args.no_autotune:
+        depth, _ = sim.autotune(5)      # z-block depth of the one-pass step (state unchanged)
     sim.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -258,7 +262,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": faces,
                        "cfl": w.cfl, "precision": "FP32 arithmetic, FP16 storage" if fp16 else "FP32",
-                       "parallelism": f"replicas x{world}",
+                       "parallelism": f"replicas x{world}", "z_block_depth": depth,
                        "l2": "inputs_larger_than_l2 (working set %.0f MB)" % (cells * (28 if fp16 else 52) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -179,6 +179,20 @@ int sbp_half_step_e(sbp_sim **sims, int nsims);
  * the events add a small gap between launches. */
 int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out);
 
+/* Autotuner of the one-pass interior step (no counterpart in the paper, whose
+ * own loops are CPU code): times the candidate z-block depths (planes per
+ * CTA, 8..256 up to the grid's interior depth) with trial_steps (>= 1) device
+ * steps each, on the simulation's stream, and keeps the fastest.  The trial
+ * steps are not committed: they write the spare field set and the current
+ * probe slot, which the next step overwrites, so the simulation's state and
+ * step index are unchanged.  The choice is remembered for this grid shape and
+ * precision and applied to simulations created later in the process.
+ * *chosen_depth and *ms_per_step (optional) receive the depth and its time.
+ * Synchronises the stream.  Errors: SBP_EINVAL, SBP_ESTATE (the grid does
+ * not run the one-pass step, or has an interface to another block),
+ * SBP_ECUDA, SBP_ETIMEOUT. */
+int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step);
+
 /* Batches: continuous batching of many simulations.  A batch advances all
  * its member simulations together, one kernel launch per kernel kind per
  * step covering every member (a tile table over the members), so many small

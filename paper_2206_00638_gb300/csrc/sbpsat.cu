@@ -24,8 +24,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "sbpsat.h"
@@ -129,6 +131,17 @@ bool desc_valid(const sbp_grid_desc *d)
     return true;
 }
 
+// z-block depths chosen by sbp_autotune, per grid shape and precision
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, int> g_tuned_depth;
+
+int tuned_depth(const sbp_grid_desc *d)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned_depth.find(std::make_tuple(d->nx, d->ny, d->nz, d->precision));
+    return it == g_tuned_depth.end() ? 0 : it->second;
+}
+
 Layout make_layout(const sbp_grid_desc *d)
 {
     Layout L;
@@ -161,6 +174,7 @@ Layout make_layout(const sbp_grid_desc *d)
         const long long target = 4ll * 2 * 152;        // about four waves of two CTAs per SM
         const long long chunks = std::max(1ll, (target + (long long)tx * ty - 1) / ((long long)tx * ty));
         int kcf = (int)std::max(8ll, ((long long)(d->nz - 5) + chunks - 1) / chunks);
+        if (const int t = tuned_depth(d)) kcf = t;
         if (const char *env = std::getenv("SBP_FUSED_KCHUNK")) {
             const int v = std::atoi(env);
             if (v > 0) kcf = v;
@@ -856,6 +870,71 @@ int check_error_flag(sbp_sim *s)
     return v ? SBP_ETIMEOUT : SBP_OK;
 }
 
+void set_depth(sbp_sim *s, int depth)
+{
+    s->fused_kchunk = depth;
+    s->fused_grid.z = (unsigned)((s->n[2] - 5 + depth - 1) / depth);
+}
+
+// Average device time of `trials` fused steps that are not committed: each
+// writes the whole new field set and this step's probe slot, both of which
+// the next real step overwrites, and the current set is left as it was.
+int time_trials(sbp_sim *s, int trials, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    const bool chain = !linked_to_other(s);
+    int rc = launch_fused_phase1(s, chain);           // warm-up of this depth
+    if (!rc && !chain) rc = launch_fused_phase2(s);
+    if (rc) return rc;
+    SBP_CUDA(cudaEventRecord(e0, s->stream));
+    for (int t = 0; t < trials; t++) {
+        if ((rc = launch_fused_phase1(s, chain))) return rc;
+        if (!chain && (rc = launch_fused_phase2(s))) return rc;
+    }
+    SBP_CUDA(cudaEventRecord(e1, s->stream));
+    SBP_CUDA(cudaEventSynchronize(e1));
+    SBP_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= (float)trials;
+    return SBP_OK;
+}
+
+int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
+{
+    if (!s->fused_ok || linked_to_other(s)) return SBP_ESTATE;
+    const int span = s->n[2] - 5;                      // interior E planes of the one-pass step
+    std::vector<int> cand;
+    for (int c : {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+        if (c <= span || cand.empty()) cand.push_back(c);
+    if (std::find(cand.begin(), cand.end(), s->fused_kchunk) == cand.end()) cand.push_back(s->fused_kchunk);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SBP_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaEventDestroy(e0);
+        return SBP_ECUDA;
+    }
+    const int keep = s->fused_kchunk;
+    int best = keep, rc = SBP_OK;
+    float best_t = 0.f;
+    for (int c : cand) {
+        set_depth(s, c);
+        float t = 0.f;
+        if ((rc = time_trials(s, trials, e0, e1, &t))) break;
+        if (best_t == 0.f || t < best_t) { best_t = t; best = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_depth(s, rc ? keep : best);
+    if (rc) return rc;
+    if ((rc = check_error_flag(s))) return rc;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned_depth[std::make_tuple(s->n[0], s->n[1], s->n[2], s->prec)] = best;
+    }
+    if (chosen) *chosen = best;
+    if (best_ms) *best_ms = best_t;
+    return SBP_OK;
+}
+
 }  // namespace
 
 // A batch: many single-block FP32 simulations advanced together, one launch
@@ -1181,6 +1260,13 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
         if (rc) return rc;
     }
     return step_timed(s, nsteps, avg_ms, launches, n_out);
+}
+
+int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step)
+{
+    if (!s || trial_steps < 1) return SBP_EINVAL;
+    cudaSetDevice(s->device);
+    return autotune(s, trial_steps, chosen_depth, ms_per_step);
 }
 
 int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples)

@@ -104,6 +104,7 @@ def lib():
                 "sbp_step_group": (I, [pp, I, I64]),
                 "sbp_half_step_h": (I, [pp, I]),
                 "sbp_half_step_e": (I, [pp, I]),
+                "sbp_autotune": (I, [P, I, C.POINTER(C.c_int), C.POINTER(D)]),
                 "sbp_step_timed": (I, [P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
                 "sbp_get_probes": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
                 "sbp_energy": (I, [P, C.POINTER(C.c_double)]),
@@ -134,7 +135,7 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
-            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
+            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_autotune", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
             "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
             "sbp_batch_create", "sbp_batch_add", "sbp_batch_remove", "sbp_batch_remaining", "sbp_batch_step",
             "sbp_batch_size", "sbp_batch_destroy", "sbp_server_create", "sbp_server_submit", "sbp_server_poll",
@@ -294,6 +295,13 @@ class Sim:
         cnt = (C.c_int64 * 5)()
         _check(lib().sbp_step_timed(self._h, int(nsteps), ms, cnt, 5), "sbp_step_timed")
         return {k: (ms[q], cnt[q]) for q, k in enumerate(self.KERNELS) if cnt[q]}
+
+    def autotune(self, trial_steps=5):
+        """Choose the z-block depth of the one-pass step by timing candidates
+        (state unchanged); returns (depth, ms per step)."""
+        depth, ms = C.c_int(), C.c_double()
+        _check(lib().sbp_autotune(self._h, int(trial_steps), C.byref(depth), C.byref(ms)), "sbp_autotune")
+        return depth.value, ms.value
 
     def sync(self):
         _check(lib().sbp_sync(self._h), "sbp_sync")
