@@ -993,6 +993,8 @@ int batch_reserve(sbp_batch *b, int n)
 }
 
 // Upload every member's parameters, prefix tables and step counters.
+constexpr int kBatchDepth = 64;   // z-planes per CTA of the batched one-pass step
+
 int batch_rebuild(sbp_batch *b)
 {
     const int n = (int)b->m.size();
@@ -1026,9 +1028,15 @@ int batch_rebuild(sbp_batch *b)
         G.cstart = s->step;
         G.probe_base = s->probe_base;
         G.cur0 = s->cur;
-        G.tiles[0] = s->fused_grid.x; G.tiles[1] = s->fused_grid.y; G.tiles[2] = s->fused_grid.z;
+        // In a batch the other grids supply the parallelism that a lone grid
+        // gets from many shallow z-blocks, so members run deep blocks (fewer
+        // halo planes re-read, fewer pipeline fills): at least kBatchDepth.
+        const int depth = std::max(s->fused_kchunk, kBatchDepth);
+        G.fp[0].kchunk = G.fp[1].kchunk = depth;
+        G.tiles[0] = s->fused_grid.x; G.tiles[1] = s->fused_grid.y;
+        G.tiles[2] = (s->n[2] - 5 + depth - 1) / depth;
         cnt[g] = s->step;
-        const long long nfg = (long long)s->fused_grid.x * s->fused_grid.y * s->fused_grid.z;
+        const long long nfg = (long long)G.tiles[0] * G.tiles[1] * G.tiles[2];
         const long long nhg = G.bh.ctas;
         const long long neg = G.be.ctas;
         if ((long long)pf[g] + nfg > INT32_MAX || (long long)ph[g] + nhg > INT32_MAX || (long long)pe[g] + neg > INT32_MAX)
