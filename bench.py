@@ -127,28 +127,30 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def csrc_digest():
+def device_digest():
+    """Digest of the device code (the two headers every kernel is compiled from)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2206_00638_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in ("kernels.cuh", "fused.cuh"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current kernels."""
+def recorded_traffic(kernel: str, workload: str, depth):
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt), if it
+    was taken on the current device code, this workload and (fused kernel) this z-depth."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as f:
             rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
     except OSError:
         return None
-    digest = csrc_digest()
+    digest = device_digest()
     for r in rows:
-        if len(r) >= 4 and r[0] == kernel and r[1] == digest:
-            return float(r[3])          # bytes per launch, scaled to the bench workload
+        if len(r) >= 5 and r[0] == kernel and r[1] == digest and r[2] == workload and r[3] in ("-", str(depth)):
+            return float(r[4])
     return None
 
 
@@ -209,8 +211,9 @@ def run_ours(args):
     nx, ny, nz = spec.n
     units = {   # cells each launch updates, and algorithmic bytes per cell
         "fused_interior": ((nx - 5) * (ny - 5) * (nz - 5), BYTES_FUSED),
-        "band_h": (cells - (nx - 4) * (ny - 4) * (nz - 4), BYTES_H),
-        "band_e": (cells - (nx - 5) * (ny - 5) * (nz - 5), BYTES_E),
+        # band kernels: nodes of the padded box outside the interior box of the one-pass step
+        "band_h": ((nx + 2) * (ny + 2) * (nz + 2) - (nx - 6) * (ny - 6) * (nz - 6), BYTES_H),
+        "band_e": ((nx + 2) * (ny + 2) * (nz + 2) - (nx - 5) * (ny - 5) * (nz - 5), BYTES_E),
         "h_update": (cells, BYTES_H),
         "e_update": (cells, BYTES_E),
     }
@@ -266,7 +269,7 @@ def run_ours(args):
                        "l2": "inputs_larger_than_l2 (working set %.0f MB)" % (cells * (28 if fp16 else 52) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": recorded_traffic(dom), "algorithmic_bytes_per_cell": bpc,
+                         "traffic": recorded_traffic(dom, w.name, depth), "algorithmic_bytes_per_cell": bpc,
                          "cells_per_launch": ucount,
                          "kernel_ms": {k: v[0] for k, v in times.items()}},
             "e2e": e2e,
