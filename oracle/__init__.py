@@ -64,6 +64,7 @@ def lib():
                 "ob_get_rhs": (V, [P, I, dp]), "ob_get_node_eps": (V, [P, I, dp]),
                 "ob_get_step": (C.c_long, [P]), "ob_set_step": (V, [P, C.c_long]),
                 "ob_connect": (I, [P, I, P, I]),
+                "ob_connect_phase": (I, [P, P, I, D]),
                 "ob_add_source": (I, [P, I, I, I, I, I, D, D, D, D]),
                 "ob_add_probe": (I, [P, I, I, I, I]),
                 "ob_probe_reserve": (V, [P, C.c_long]), "ob_get_probes": (V, [P, dp]),
@@ -221,6 +222,14 @@ def connect(a: Block, face_a: int, b: Block, face_b: int) -> None:
     rc = lib().ob_connect(a._h, face_a, b._h, face_b)
     if rc != 0:
         raise ValueError(f"faces do not conform (code {rc})")
+
+
+def connect_phase(re: Block, im: Block, axis: int, alpha: float) -> None:
+    """Periodic faces along ``axis`` with phase shift ``alpha`` (radians per period,
+    Eqs. (EPBC1-6)) for the complex field re + j im; both blocks are stepped together."""
+    rc = lib().ob_connect_phase(re._h, im._h, int(axis), float(alpha))
+    if rc != 0:
+        raise ValueError(f"blocks do not form a complex pair (code {rc})")
 
 
 def step(blocks, nsteps: int) -> None:

@@ -15,6 +15,12 @@
  *   - block interface SAT: the periodic SAT of Eqs. (EPBC1-6) with
  *     zero phase and the +-1/2 coefficients of Eq. (EPBCP), coupling one
  *     block face to another block's face (conforming)
+ *   - periodic SAT with a phase shift (Eqs. (EPBC1-6)): a complex field is
+ *     a pair of blocks (real part, imaginary part); the penalty at a high
+ *     face compares with e^{-j alpha} times the low-face field, at a low
+ *     face with e^{+j alpha} times the high-face field, so each face's
+ *     partner value is w_a (partner) + w_b (second partner) with
+ *     (w_a, w_b) = (cos alpha, +-sin alpha)
  *   - absorbing SAT: first-order characteristic (Silver-Mueller) penalty,
  *     not in the paper (it uses CPML); energy-dissipative by construction
  *   - leapfrog in time, U^n = [E^n, H^{n-1/2}]                       Sec. IV, Sec. V
@@ -161,6 +167,8 @@ typedef struct ob_block {
     int face[6];                 /* x-, x+, y-, y+, z-, z+ */
     struct ob_block *nbr[6];
     int nbr_face[6];
+    struct ob_block *nbr2[6];    /* second partner of a phase-shifted periodic face (NULL: none) */
+    double nbr_w[6][2];          /* partner value = w[0] nbr + w[1] nbr2 */
     double *cell_eps, *cell_mu;  /* relative, n0*n1*n2, x fastest */
     double *F[6];                /* fields, natural extents */
     double *epsn[6], *mun[6];    /* relative node eps, mu on each component grid */
@@ -229,7 +237,10 @@ ob_block *ob_create(int nx, int ny, int nz, double dx, double dy, double dz, dou
     b->n[0] = nx; b->n[1] = ny; b->n[2] = nz;
     b->h[0] = dx; b->h[1] = dy; b->h[2] = dz;
     b->dt = dt;
-    for (int f = 0; f < 6; f++) { b->face[f] = faces[f]; b->nbr[f] = NULL; b->nbr_face[f] = -1; }
+    for (int f = 0; f < 6; f++) {
+        b->face[f] = faces[f]; b->nbr[f] = NULL; b->nbr_face[f] = -1;
+        b->nbr2[f] = NULL; b->nbr_w[f][0] = 1.0; b->nbr_w[f][1] = 0.0;
+    }
     size_t ncell = (size_t)nx * ny * nz;
     if (eps_cells) { b->cell_eps = (double *)malloc(ncell * sizeof(double)); memcpy(b->cell_eps, eps_cells, ncell * sizeof(double)); }
     if (mu_cells) { b->cell_mu = (double *)malloc(ncell * sizeof(double)); memcpy(b->cell_mu, mu_cells, ncell * sizeof(double)); }
@@ -283,6 +294,36 @@ int ob_connect(ob_block *a, int fa, ob_block *b, int fb)
     a->face[fa] = OB_IFACE; b->face[fb] = OB_IFACE;
     a->nbr[fa] = b; a->nbr_face[fa] = fb;
     b->nbr[fb] = a; b->nbr_face[fb] = fa;
+    a->nbr2[fa] = NULL; a->nbr_w[fa][0] = 1.0; a->nbr_w[fa][1] = 0.0;
+    b->nbr2[fb] = NULL; b->nbr_w[fb][0] = 1.0; b->nbr_w[fb][1] = 0.0;
+    return 0;
+}
+
+/* Periodic faces along `axis` with phase shift alpha (Eqs. (EPBC1-6)) for the
+ * complex field re + j im held by two blocks of equal shape.  The field one
+ * period above equals e^{-j alpha} times the field here, so
+ *   high face:  C_high - e^{-j alpha} C_low,   low face:  C_low - e^{+j alpha} C_high
+ * (C the partner component).  With e^{-+j alpha}(a + j b) split into real and
+ * imaginary parts, the partner value seen by
+ *   re, high: cos a * re_low  + sin a * im_low      re, low: cos a * re_high - sin a * im_high
+ *   im, high: cos a * im_low  - sin a * re_low      im, low: cos a * im_high + sin a * re_high */
+int ob_connect_phase(ob_block *re, ob_block *im, int axis, double alpha)
+{
+    if (axis < 0 || axis > 2 || re == im) return -1;
+    for (int t = 0; t < 3; t++)
+        if (re->n[t] != im->n[t] || re->h[t] != im->h[t]) return -2;
+    const double c = cos(alpha), s = sin(alpha);
+    const int lo = 2 * axis, hi = 2 * axis + 1;
+    ob_block *own[2] = {re, im}, *other[2] = {im, re};
+    const double wb_hi[2] = {+s, -s}, wb_lo[2] = {-s, +s};
+    for (int q = 0; q < 2; q++) {
+        ob_block *b = own[q];
+        b->face[lo] = OB_IFACE; b->face[hi] = OB_IFACE;
+        b->nbr[hi] = b; b->nbr_face[hi] = lo; b->nbr2[hi] = other[q];
+        b->nbr_w[hi][0] = c; b->nbr_w[hi][1] = wb_hi[q];
+        b->nbr[lo] = b; b->nbr_face[lo] = hi; b->nbr2[lo] = other[q];
+        b->nbr_w[lo][0] = c; b->nbr_w[lo][1] = wb_lo[q];
+    }
     return 0;
 }
 
@@ -411,7 +452,9 @@ static void sat_terms(const ob_block *b, int c, const int idx[3], double eps_r, 
             int nside = (nf % 2) ? +1 : -1;
             int q[3] = {idx[0], idx[1], idx[2]};
             q[ax] = (nside < 0) ? 0 : ext(nb, p, ax) - 1;
-            double nv = nb->F[p][at(nb, p, q[0], q[1], q[2])];
+            const size_t qo = at(nb, p, q[0], q[1], q[2]);
+            double nv = b->nbr_w[f][0] * nb->F[p][qo];
+            if (b->nbr2[f]) nv += b->nbr_w[f][1] * b->nbr2[f]->F[p][qo];
             *expl += phi * ratio * 0.5 * (pv - nv);
         }
     }

@@ -78,3 +78,39 @@ class Pair1D:
             if probe_e is not None:
                 out.append(self.E[probe_e])
         return np.array(out)
+
+
+class PeriodicPair1D:
+    """The pair (Ex, Hy) along z with the phase-shifted periodic SAT of Eqs. (EPBC2),
+    (EPBC4) and the coefficients of Eq. (EPBCP), complex, dense (printed matrices).
+    The field one period up equals e^{-j alpha} times the field here."""
+
+    def __init__(self, n, h, dt, alpha):
+        self.n, self.h, self.dt = n, h, dt
+        Pp = h * appendix.p_plus(n)
+        Pm = h * appendix.p_minus(n)
+        Dp = np.linalg.solve(np.diag(Pp), appendix.q_plus(n))
+        Dm = np.linalg.solve(np.diag(Pm), appendix.q_minus(n))
+        s = -1.0
+        AE = (s * Dp).astype(complex)
+        AH = (s * Dm).astype(complex)
+        ph_hi = np.exp(-1j * alpha)      # high face compares with e^{-j alpha} x low face
+        ph_lo = np.exp(+1j * alpha)      # low face compares with e^{+j alpha} x high face
+        for side in (-1, +1):
+            coef = 0.5 * (-s * side)     # sigma / chi of Eq. (EPBCP) for this pair and face
+            ie, ih = (0, 0) if side < 0 else (n, n + 1)
+            je, jh = (n, n + 1) if side < 0 else (0, 0)
+            ph = ph_lo if side < 0 else ph_hi
+            AE[ie, ih] += coef / Pp[ie]
+            AE[ie, jh] -= coef * ph / Pp[ie]
+            AH[ih, ie] += coef / Pm[ih]
+            AH[ih, je] -= coef * ph / Pm[ih]
+        self.AE = AE / EPS0
+        self.AH = AH / MU0
+        self.E = np.zeros(n + 1, complex)
+        self.H = np.zeros(n + 2, complex)
+
+    def step(self, nsteps):
+        for _ in range(nsteps):
+            self.H = self.H + self.dt * (self.AH @ self.E)
+            self.E = self.E + self.dt * (self.AE @ self.H)
