@@ -118,6 +118,19 @@ int sbp_create_in(const sbp_grid_desc *desc, void *cuda_stream, void *dev_worksp
  * sbp_step_group and share one stream. */
 int sbp_connect(sbp_sim *a, int face_a, sbp_sim *b, int face_b);
 
+/* Periodic boundary with a phase shift (Eqs. (EPBC1)-(EPBC6), coefficients of
+ * Eq. (EPBCP)) along `axis` (0..2) for the complex field re + j im held by two
+ * simulations of equal shape, spacing, dt, precision, stream and FP16 scales.
+ * The field one period up equals e^{-j alpha} times the field here (alpha =
+ * k0_axis * L_axis, radians): a high face is penalised towards e^{-j alpha}
+ * times the low-face field, a low face towards e^{+j alpha} times the
+ * high-face field, each split into its real and imaginary parts.  Both faces
+ * of the axis become SBP_INTERFACE in both simulations; call once per
+ * periodic axis, and advance the pair together with sbp_step_group.  alpha = 0
+ * gives the zero-phase periodic SAT of sbp_connect(s, hi, s, lo) in each part.
+ * Errors: SBP_EINVAL, SBP_ENOTCONFORMING. */
+int sbp_connect_phase(sbp_sim *re, sbp_sim *im, int axis, double alpha);
+
 /* Copy one component (natural extents, x fastest) into the simulation.
  * src: host pointer (is_device = 0, copied before return) or device pointer
  * (is_device = 1, read asynchronously on the simulation's stream). */

@@ -59,6 +59,8 @@ template <typename T> struct Coef { T hi, lo; };
 
 struct Link {               // interface partner of one face
     const void *F[6];       // partner block's padded fields
+    const void *G[6];       // second partner (phase-shifted periodic face of a complex pair), or null
+    double w[2];            // partner value = w[0] F + w[1] G (used when G is set)
     long long sy, sz;       // partner strides (elements)
     int n_norm;             // partner cell count along the face normal
     int side;               // partner face side: -1 low, +1 high
@@ -396,7 +398,10 @@ __device__ __forceinline__ T h_apply(const Params<T, S> &p, const int idx[3], lo
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
                     for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
-                    acc.add(p.B[a], pv - ld_s(nf + on), phi);
+                    T nv = ld_s(nf + on);
+                    if (L.G[u])   // e^{-+j alpha} times the complex partner, split into parts
+                        nv = T(L.w[0]) * nv + T(L.w[1]) * ld_s(static_cast<const S *>(L.G[u]) + on);
+                    acc.add(p.B[a], pv - nv, phi);
                 }
             }
         }
@@ -477,7 +482,10 @@ __device__ __forceinline__ T e_apply(const Params<T, S> &p, const int idx[3], lo
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
                     for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
-                    acc.add(p.A[a], pv - ldf<CG>(nf + on), phi);
+                    T nv = ldf<CG>(nf + on);
+                    if (L.G[u])
+                        nv = T(L.w[0]) * nv + T(L.w[1]) * ldf<CG>(static_cast<const S *>(L.G[u]) + on);
+                    acc.add(p.A[a], pv - nv, phi);
                 }
             }
         }

@@ -79,6 +79,8 @@ struct sbp_sim {
     double *escalar = nullptr;
     sbp_sim *nbr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int nbr_face[6] = {-1, -1, -1, -1, -1, -1};
+    sbp_sim *nbr2[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};   // phase pair partner
+    double nbr_w[6][2] = {{1, 0}, {1, 0}, {1, 0}, {1, 0}, {1, 0}, {1, 0}};
     std::vector<sbp::Src> src;
     std::vector<sbp::Prb> prb;
     void *probe_buf = nullptr;
@@ -386,6 +388,13 @@ int make_params(const sbp_sim *s, sbp::Params<T, S> &p, int eset, int hset)
             const int nh = nb->fused_step ? nb->cur ^ 1 : nb->cur;
             for (int c = 0; c < 3; c++) p.link[f].F[c] = nb->set[nb->cur][c];
             for (int c = 3; c < 6; c++) p.link[f].F[c] = nb->set[nh][c];
+            if (const sbp_sim *n2 = s->nbr2[f]) {
+                const int nh2 = n2->fused_step ? n2->cur ^ 1 : n2->cur;
+                for (int c = 0; c < 3; c++) p.link[f].G[c] = n2->set[n2->cur][c];
+                for (int c = 3; c < 6; c++) p.link[f].G[c] = n2->set[nh2][c];
+                p.link[f].w[0] = s->nbr_w[f][0];
+                p.link[f].w[1] = s->nbr_w[f][1];
+            }
             p.link[f].sy = nb->sy;
             p.link[f].sz = nb->sz;
             p.link[f].n_norm = nb->n[f / 2];
@@ -605,7 +614,7 @@ int launch_fused_phase2(sbp_sim *s) { return launch_band_e(s, s->stream); }
 bool linked_to_other(const sbp_sim *s)
 {
     for (int f = 0; f < 6; f++)
-        if (s->face[f] == SBP_INTERFACE && s->nbr[f] && s->nbr[f] != s) return true;
+        if (s->face[f] == SBP_INTERFACE && ((s->nbr[f] && s->nbr[f] != s) || s->nbr2[f])) return true;
     return false;
 }
 
@@ -1115,6 +1124,32 @@ int sbp_connect(sbp_sim *a, int fa, sbp_sim *b, int fb)
     if (a->fscale[0] != b->fscale[0] || a->fscale[1] != b->fscale[1]) return SBP_EINVAL;
     a->face[fa] = SBP_INTERFACE; a->nbr[fa] = b; a->nbr_face[fa] = fb;
     b->face[fb] = SBP_INTERFACE; b->nbr[fb] = a; b->nbr_face[fb] = fa;
+    a->nbr2[fa] = nullptr; a->nbr_w[fa][0] = 1.0; a->nbr_w[fa][1] = 0.0;
+    b->nbr2[fb] = nullptr; b->nbr_w[fb][0] = 1.0; b->nbr_w[fb][1] = 0.0;
+    return SBP_OK;
+}
+
+int sbp_connect_phase(sbp_sim *re, sbp_sim *im, int axis, double alpha)
+{
+    if (!re || !im || re == im || axis < 0 || axis > 2 || !std::isfinite(alpha)) return SBP_EINVAL;
+    if (re->prec != im->prec || re->stream != im->stream || re->dt != im->dt) return SBP_EINVAL;
+    if (re->fscale[0] != im->fscale[0] || re->fscale[1] != im->fscale[1]) return SBP_EINVAL;
+    for (int t = 0; t < 3; t++)
+        if (re->n[t] != im->n[t] || re->h[t] != im->h[t]) return SBP_ENOTCONFORMING;
+    // the field one period up is e^{-j alpha} times the field here: a high face
+    // compares with e^{-j alpha} (low face), a low face with e^{+j alpha} (high face)
+    const double c = std::cos(alpha), sn = std::sin(alpha);
+    const int lo = 2 * axis, hi = 2 * axis + 1;
+    sbp_sim *own[2] = {re, im}, *other[2] = {im, re};
+    const double wb_hi[2] = {+sn, -sn}, wb_lo[2] = {-sn, +sn};
+    for (int q = 0; q < 2; q++) {
+        sbp_sim *s = own[q];
+        s->face[lo] = SBP_INTERFACE; s->face[hi] = SBP_INTERFACE;
+        s->nbr[hi] = s; s->nbr_face[hi] = lo; s->nbr2[hi] = other[q];
+        s->nbr_w[hi][0] = c; s->nbr_w[hi][1] = wb_hi[q];
+        s->nbr[lo] = s; s->nbr_face[lo] = hi; s->nbr2[lo] = other[q];
+        s->nbr_w[lo][0] = c; s->nbr_w[lo][1] = wb_lo[q];
+    }
     return SBP_OK;
 }
 

@@ -105,6 +105,7 @@ def lib():
                 "sbp_half_step_h": (I, [pp, I]),
                 "sbp_half_step_e": (I, [pp, I]),
                 "sbp_autotune": (I, [P, I, C.POINTER(C.c_int), C.POINTER(D)]),
+                "sbp_connect_phase": (I, [P, P, I, D]),
                 "sbp_step_timed": (I, [P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
                 "sbp_get_probes": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
                 "sbp_energy": (I, [P, C.POINTER(C.c_double)]),
@@ -133,7 +134,7 @@ def lib():
 
 
 def exported_symbols() -> Sequence[str]:
-    return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_set_field",
+    return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_connect_phase", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
             "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_autotune", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
             "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
@@ -367,6 +368,12 @@ def energy_group(sims):
     w = C.c_double()
     _check(lib().sbp_energy_group(_handles(sims), len(sims), C.byref(w)), "sbp_energy_group")
     return w.value
+
+
+def connect_phase(re: "Sim", im: "Sim", axis: int, alpha: float) -> None:
+    """Periodic faces along ``axis`` with phase shift ``alpha`` for the complex field
+    re + j im (two simulations advanced together with ``step_group``)."""
+    _check(lib().sbp_connect_phase(re.handle, im.handle, int(axis), float(alpha)), "sbp_connect_phase")
 
 
 def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_every=0, field_scale=(0.0, 0.0)):
