@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=512, help="serving workload: number of requests")
     ap.add_argument("--rho", type=float, default=0.9, help="serving workload: offered load / plain throughput")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default z-block depth")
+    ap.add_argument("--scheme", choices=["sbp", "fdtd"], default="sbp",
+                    help="fdtd: the plain Yee comparator on the same grid and kernels (PEC workloads)")
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--budget-gib", type=float, default=8.0)
     return ap.parse_args()
@@ -177,11 +179,12 @@ def run_ours(args):
     spec = w.blocks[0]
     cells = spec.n[0] * spec.n[1] * spec.n[2]
     stream = torch.cuda.current_stream()
-    sim = sbpsat.from_workload(w, stream=stream, precision=prec)[0]
+    flags = sbpsat.FLAG_FDTD if args.scheme == "fdtd" else 0
+    sim = sbpsat.from_workload(w, stream=stream, precision=prec, flags=flags)[0]
     sim.reserve_probes(args.warmup + args.steps + min(args.steps, 400) + 8)
     depth = None
     if not args.no_autotune:
-        depth, _ = sim.autotune(5)      # z-block depth of the one-pass step (state unchanged)
+        depth, _ = sim.autotune(20)     # z-block depth of the one-pass step (state unchanged)
     sim.step(args.warmup)
     torch.cuda.synchronize()
 
@@ -234,7 +237,8 @@ def run_ours(args):
         out = torch.empty(pinned[2].shape, dtype=torch.float32).pin_memory()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = sbpsat.Sim(spec.n, spec.h, spec.faces, eps_r=spec.eps_r, cfl=w.cfl, stream=stream, precision=prec)
+        s2 = sbpsat.Sim(spec.n, spec.h, spec.faces, eps_r=spec.eps_r, cfl=w.cfl, stream=stream, precision=prec,
+                        flags=flags)
         for c in range(6):
             sbpsat._check(sbpsat.lib().sbp_set_field(s2.handle, c, pinned[c].data_ptr(), 0), "set")
         for src in spec.sources:
@@ -266,6 +270,7 @@ def run_ours(args):
             "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": faces,
                        "cfl": w.cfl, "precision": "FP32 arithmetic, FP16 storage" if fp16 else "FP32",
                        "parallelism": f"replicas x{world}", "z_block_depth": depth,
+                       "scheme": "SBP-SAT" if args.scheme == "sbp" else "FDTD (Yee) comparator",
                        "l2": "inputs_larger_than_l2 (working set %.0f MB)" % (cells * (28 if fp16 else 52) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,

@@ -59,6 +59,16 @@ typedef enum { SBP_EX = 0, SBP_EY = 1, SBP_EZ = 2, SBP_HX = 3, SBP_HY = 4, SBP_H
 typedef enum { SBP_GAUSS = 0, SBP_GAUSS_DERIV = 1, SBP_MOD_GAUSS = 2 } sbp_waveform_t;
 
 #define SBP_FLAG_ALLOW_UNSTABLE 1  /* accept cfl_fraction > 1 (for stability tests) */
+/* The FDTD comparator: the plain Yee scheme with strong PEC walls on the same
+ * grid, arrays and kernels (the method the paper measures its overhead
+ * against, Sec. VI).  H is updated on the half nodes of its minus-grid axes
+ * (the SBP boundary nodes 0 and n+1 keep their value), E on the half nodes and
+ * the interior nodes 1..n-1 of its plus-grid axes (tangential E on the walls
+ * keeps its value, zero unless set); every difference is the two-point row and
+ * no SAT applies.  Requires six PEC faces, FP32 or FP16 storage, uniform mu,
+ * >= 8 cells per axis and energy_every = 0; the energy, half-step, batch and
+ * interface calls return SBP_ESTATE or SBP_EINVAL for such a simulation. */
+#define SBP_FLAG_FDTD 2
 
 /* Problem statement of one block (Sec. V: a cavity of nx*ny*nz cells; Sec. VI:
  * mesh size, materials, walls, dt at a fraction of the CFL limit). */

@@ -480,6 +480,60 @@ __device__ __forceinline__ void band_h_at(const Params<T, S> &p, const int idx[3
     if (have[2]) st_s(outs[2] + o, hn[2] = quant<S>(h_apply<T, 5, MUVAR, G>(p, idx, o, hz, vz)));
 }
 
+// Yee FDTD comparator (the FDTD method the paper measures its overhead
+// against, with strong PEC walls) on the same grid: H exists on the half nodes
+// 1..n of its minus-grid axes (the SBP boundary nodes 0 and n+1 are not part
+// of it), E on the half nodes 1..n of its minus-grid axes and the interior
+// nodes 1..n-1 of its plus-grid axes (tangential E on a wall stays zero); every
+// row is the two-point row and no SAT applies.  Nodes outside the Yee set keep
+// their value (copied to the new set).
+template <int C>
+__device__ __forceinline__ bool yee_node(const int idx[3], const int n[3])
+{
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        in = in && idx[a] >= 1 && idx[a] <= (on_plus(C, a) ? n[a] - 1 : n[a]);
+    return in;
+}
+
+template <typename T, bool MUVAR, int C, typename S>
+__device__ __forceinline__ void yee_h(const Params<T, S> &p, const int idx[3], long long o, bool have, S *out, T &hn)
+{
+    if (!have) return;
+    const T hold = ld_s(p.F[C] + o);
+    // H on its plus-grid axis is a face-normal component: nodes 0..n all exist
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+        if (!on_plus(C, a)) in = in && idx[a] >= 1 && idx[a] <= p.n[a];
+    if (in) {
+        Tri<T> v[2];
+        h_gather<T, C, 0>(p, idx, o, v);
+        hn = quant<S>(h_apply<T, C, MUVAR, 0>(p, idx, o, hold, v));
+    } else {
+        hn = hold;
+    }
+    st_s(out + o, hn);
+}
+
+template <typename T, bool MUVAR, int C, typename S>
+__device__ __forceinline__ void yee_e(const Params<T, S> &p, const int idx[3], long long o, bool have, unsigned sm,
+                                      double t_half, S *out, T &en)
+{
+    if (!have) return;
+    const T eold = ld_s(p.F[C] + o);
+    if (yee_node<C>(idx, p.n)) {
+        Tri<T> v[2];
+        e_gather<T, C, false, 0>(p, idx, o, v);
+        const T se = cell_sum<C, T>(p.eps, o, p.sy, p.sz);
+        en = quant<S>(e_apply<T, C, MUVAR, false, 0>(p, idx, o, eold, se, v, sm, t_half));
+    } else {
+        en = eold;
+    }
+    st_s(out + o, en);
+}
+
 // H^{n+1/2} at the nodes of band warp w: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
 template <typename T, bool MUVAR, typename S>
 __device__ __forceinline__ void band_h_warp(const Params<T, S> &p, const Band &b, unsigned w, int lane, long long pslot,
@@ -495,12 +549,18 @@ __device__ __forceinline__ void band_h_warp(const Params<T, S> &p, const Band &b
     T hn[3];
     const bool have[3] = {i <= nx && j <= ny + 1 && k <= nz + 1, i <= nx + 1 && j <= ny && k <= nz + 1,
                           i <= nx + 1 && j <= ny + 1 && k <= nz};
-    switch (G) {   // uniform per warp
-    case 4: band_h_at<T, MUVAR, 4>(p, idx, o, have, outs, hn); break;
-    case 2: band_h_at<T, MUVAR, 2>(p, idx, o, have, outs, hn); break;
-    case 6: band_h_at<T, MUVAR, 6>(p, idx, o, have, outs, hn); break;
-    case 1: band_h_at<T, MUVAR, 1>(p, idx, o, have, outs, hn); break;
-    default: band_h_at<T, MUVAR, 7>(p, idx, o, have, outs, hn); break;
+    if (p.fdtd) {
+        yee_h<T, MUVAR, 3>(p, idx, o, have[0], outs[0], hn[0]);
+        yee_h<T, MUVAR, 4>(p, idx, o, have[1], outs[1], hn[1]);
+        yee_h<T, MUVAR, 5>(p, idx, o, have[2], outs[2], hn[2]);
+    } else {
+        switch (G) {   // uniform per warp
+        case 4: band_h_at<T, MUVAR, 4>(p, idx, o, have, outs, hn); break;
+        case 2: band_h_at<T, MUVAR, 2>(p, idx, o, have, outs, hn); break;
+        case 6: band_h_at<T, MUVAR, 6>(p, idx, o, have, outs, hn); break;
+        case 1: band_h_at<T, MUVAR, 1>(p, idx, o, have, outs, hn); break;
+        default: band_h_at<T, MUVAR, 7>(p, idx, o, have, outs, hn); break;
+        }
     }
     if (pm) band_probes(p, pm, 3, i, j, pslot, hn, have);
 }
@@ -564,12 +624,18 @@ __device__ __forceinline__ void band_e_warp(const Params<T, S> &p, const Band &b
     T en[3];
     const bool have[3] = {i <= nx + 1 && j <= ny && k <= nz, i <= nx && j <= ny + 1 && k <= nz,
                           i <= nx && j <= ny && k <= nz + 1};
-    switch (G) {   // uniform per warp
-    case 4: band_e_at<T, MUVAR, 4>(p, idx, o, have, sm, t_half, outs, en); break;
-    case 2: band_e_at<T, MUVAR, 2>(p, idx, o, have, sm, t_half, outs, en); break;
-    case 6: band_e_at<T, MUVAR, 6>(p, idx, o, have, sm, t_half, outs, en); break;
-    case 1: band_e_at<T, MUVAR, 1>(p, idx, o, have, sm, t_half, outs, en); break;
-    default: band_e_at<T, MUVAR, 7>(p, idx, o, have, sm, t_half, outs, en); break;
+    if (p.fdtd) {
+        yee_e<T, MUVAR, 0>(p, idx, o, have[0], sm, t_half, outs[0], en[0]);
+        yee_e<T, MUVAR, 1>(p, idx, o, have[1], sm, t_half, outs[1], en[1]);
+        yee_e<T, MUVAR, 2>(p, idx, o, have[2], sm, t_half, outs[2], en[2]);
+    } else {
+        switch (G) {   // uniform per warp
+        case 4: band_e_at<T, MUVAR, 4>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 2: band_e_at<T, MUVAR, 2>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 6: band_e_at<T, MUVAR, 6>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 1: band_e_at<T, MUVAR, 1>(p, idx, o, have, sm, t_half, outs, en); break;
+        default: band_e_at<T, MUVAR, 7>(p, idx, o, have, sm, t_half, outs, en); break;
+        }
     }
     if (pm) band_probes(p, pm, 0, i, j, pslot, en, have);
 }

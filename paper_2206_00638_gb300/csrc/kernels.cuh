@@ -104,6 +104,7 @@ struct Params {
     long long step;                    // n: the E half-step injects J(t^{n+1/2})
     double *partials;                  // energy partial sums, one per CTA of h_update
     int kchunk;
+    int fdtd;                          // 1: plain Yee FDTD comparator (band kernels only)
 };
 
 // ---------------------------------------------------------------------------

@@ -52,6 +52,7 @@ struct sbp_sim {
     int face[6] = {0, 0, 0, 0, 0, 0};
     int energy_every = 0;
     int flags = 0;
+    bool fdtd = false;                    // Yee FDTD comparator (SBP_FLAG_FDTD)
     int device = 0;
     cudaStream_t stream = nullptr;
     size_t esize = 4;                     // bytes per stored field element
@@ -123,6 +124,13 @@ bool desc_valid(const sbp_grid_desc *d)
     for (int f = 0; f < 6; f++)
         if (d->face[f] < SBP_PEC || d->face[f] > SBP_INTERFACE) return false;
     if (d->energy_every < 0) return false;
+    if (d->flags & ~(SBP_FLAG_ALLOW_UNSTABLE | SBP_FLAG_FDTD)) return false;
+    if (d->flags & SBP_FLAG_FDTD) {
+        for (int f = 0; f < 6; f++)
+            if (d->face[f] != SBP_PEC) return false;
+        if (d->energy_every != 0 || d->precision == SBP_FP64 || d->mu_r || d->nx < 8 || d->ny < 8 || d->nz < 8)
+            return false;
+    }
     const long long cells = (long long)d->nx * d->ny * d->nz;
     if (cells > (1ll << 34)) return false;
     for (const float *m : {d->eps_r, d->mu_r}) {
@@ -268,6 +276,8 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     for (int f = 0; f < 6; f++) s->face[f] = d->face[f];
     s->energy_every = d->energy_every;
     s->flags = d->flags;
+    s->fdtd = (d->flags & SBP_FLAG_FDTD) != 0;
+    if (s->fdtd && !L.fused) return SBP_EINVAL;   // the comparator runs in the one-pass + band kernels only
     s->esize = L.esize;
     s->psize = d->precision == SBP_FP64 ? 8 : 4;
     if (d->precision == SBP_FP32_FP16STORE) {
@@ -429,6 +439,7 @@ int make_params(const sbp_sim *s, sbp::Params<T, S> &p, int eset, int hset)
     p.step = s->step;
     p.partials = s->partials;
     p.kchunk = s->kchunk;
+    p.fdtd = s->fdtd ? 1 : 0;
     return SBP_OK;
 }
 
@@ -1113,6 +1124,7 @@ int sbp_create_in(const sbp_grid_desc *desc, void *cuda_stream, void *dev_worksp
 int sbp_connect(sbp_sim *a, int fa, sbp_sim *b, int fb)
 {
     if (!a || !b || fa < 0 || fa > 5 || fb < 0 || fb > 5) return SBP_EINVAL;
+    if (a->fdtd || b->fdtd) return SBP_EINVAL;
     if (a->prec != b->prec || a->stream != b->stream) return SBP_EINVAL;
     const int ax = fa / 2;
     if (fb / 2 != ax || (fa % 2) == (fb % 2)) return SBP_ENOTCONFORMING;
@@ -1132,6 +1144,7 @@ int sbp_connect(sbp_sim *a, int fa, sbp_sim *b, int fb)
 int sbp_connect_phase(sbp_sim *re, sbp_sim *im, int axis, double alpha)
 {
     if (!re || !im || re == im || axis < 0 || axis > 2 || !std::isfinite(alpha)) return SBP_EINVAL;
+    if (re->fdtd || im->fdtd) return SBP_EINVAL;
     if (re->prec != im->prec || re->stream != im->stream || re->dt != im->dt) return SBP_EINVAL;
     if (re->fscale[0] != im->fscale[0] || re->fscale[1] != im->fscale[1]) return SBP_EINVAL;
     for (int t = 0; t < 3; t++)
@@ -1283,12 +1296,18 @@ int sbp_step_group(sbp_sim **sims, int nsims, int64_t nsteps)
 int sbp_half_step_h(sbp_sim **sims, int nsims)
 {
     int rc = check_group(sims, nsims);
+    if (!rc)
+        for (int q = 0; q < nsims; q++)
+            if (sims[q]->fdtd) return SBP_ESTATE;
     return rc ? rc : half_h(sims, nsims);
 }
 
 int sbp_half_step_e(sbp_sim **sims, int nsims)
 {
     int rc = check_group(sims, nsims);
+    if (!rc)
+        for (int q = 0; q < nsims; q++)
+            if (sims[q]->fdtd) return SBP_ESTATE;
     return rc ? rc : half_e(sims, nsims);
 }
 
@@ -1340,6 +1359,7 @@ int sbp_energy_group(sbp_sim **sims, int nsims, double *W)
     for (int q = 0; q < nsims; q++) {
         sbp_sim *s = sims[q];
         if (!s) return SBP_EINVAL;
+        if (s->fdtd) return SBP_ESTATE;   // the energy of Eq. (16) is not the Yee scheme's
         cudaSetDevice(s->device);
         int rc = launch_h_any(s, true, false);
         if (rc) return rc;
@@ -1363,6 +1383,7 @@ int sbp_energy(sbp_sim *s, double *W)
 int sbp_energy_noalloc(sbp_sim *s, double *W_dev)
 {
     if (!s || !W_dev) return SBP_EINVAL;
+    if (s->fdtd) return SBP_ESTATE;
     if (s->npartials > SBP_NOALLOC_MAX_PARTIALS) {
         std::fprintf(stderr, "sbp_energy_noalloc: grid needs %lld partial sums, limit %d\n",
                      s->npartials, SBP_NOALLOC_MAX_PARTIALS);
@@ -1450,7 +1471,8 @@ int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
 int sbp_batch_add(sbp_batch *b, sbp_sim *s, int64_t nsteps)
 {
     if (!b || !s || nsteps < 0) return SBP_EINVAL;
-    if (!s->fused_ok || s->prec != SBP_FP32 || s->stream != b->stream || s->energy_every > 0 || s->device != b->device)
+    if (!s->fused_ok || s->prec != SBP_FP32 || s->fdtd || s->stream != b->stream || s->energy_every > 0 ||
+        s->device != b->device)
         return SBP_EINVAL;
     for (int f = 0; f < 6; f++)
         if (s->face[f] == SBP_INTERFACE) return SBP_EINVAL;

@@ -32,6 +32,7 @@ FP32, FP64, FP32_FP16STORE = 0, 1, 2
 EX, EY, EZ, HX, HY, HZ = range(6)
 GAUSS, GAUSS_DERIV, MOD_GAUSS = 0, 1, 2
 FLAG_ALLOW_UNSTABLE = 1
+FLAG_FDTD = 2          # plain Yee FDTD comparator (six PEC faces, one-pass path)
 
 ON_PLUS = ((0, 1, 1), (1, 0, 1), (1, 1, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))
 
@@ -376,13 +377,15 @@ def connect_phase(re: "Sim", im: "Sim", axis: int, alpha: float) -> None:
     _check(lib().sbp_connect_phase(re.handle, im.handle, int(axis), float(alpha)), "sbp_connect_phase")
 
 
-def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_every=0, field_scale=(0.0, 0.0)):
+def from_workload(w, precision=FP32, stream=None, torch_memory=True, energy_every=0, field_scale=(0.0, 0.0),
+                  flags=0):
     """Create the GPU blocks of a workloads.Workload (fields, sources, probes, links).
-    field_scale: (E, H) scales of FP16 storage (0 = library default)."""
+    field_scale: (E, H) scales of FP16 storage (0 = library default); flags: FLAG_*."""
     sims = []
     for b in w.blocks:
         s = Sim(b.n, b.h, b.faces, eps_r=b.eps_r, mu_r=b.mu_r, cfl=w.cfl, precision=precision,
-                stream=stream, torch_memory=torch_memory, energy_every=energy_every, field_scale=field_scale)
+                stream=stream, torch_memory=torch_memory, energy_every=energy_every, field_scale=field_scale,
+                flags=flags)
         if b.fields is not None:
             for c in range(6):
                 s.set_field(c, b.fields[c])
