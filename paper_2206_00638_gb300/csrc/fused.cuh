@@ -223,6 +223,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         issue_plane<S>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
         ++issued;
     }
+#pragma unroll(sizeof(S) == 4 ? 2 : 1)   // two planes per iteration with FP32 storage (faster there, slower with FP16)
     for (int q = k0; q <= k1 && !aborted; ++q) {
         const int iq = q - k0 + 1;                   // load index of plane q
         const int sq = iq % kStages;
