@@ -69,6 +69,12 @@ typedef enum { SBP_GAUSS = 0, SBP_GAUSS_DERIV = 1, SBP_MOD_GAUSS = 2 } sbp_wavef
  * >= 8 cells per axis and energy_every = 0; the energy, half-step, batch and
  * interface calls return SBP_ESTATE or SBP_EINVAL for such a simulation. */
 #define SBP_FLAG_FDTD 2
+/* Test hook for failure detection: the one-pass step issues no plane loads,
+ * so each of its bounded pipeline waits runs out (after a short limit); every
+ * CTA raises the device error flag and exits, and the next synchronising call
+ * (sbp_sync, sbp_get_field to the host, sbp_save) returns SBP_ETIMEOUT.  The
+ * CUDA context stays usable.  Only meaningful for grids on the one-pass path. */
+#define SBP_FLAG_TEST_WAIT_TIMEOUT 4
 
 /* Problem statement of one block (Sec. V: a cavity of nx*ny*nz cells; Sec. VI:
  * mesh size, materials, walls, dt at a fraction of the CFL limit). */
@@ -330,6 +336,19 @@ int sbp_energy_series(sbp_sim *s, double *out, int64_t cap, int64_t *count);
 
 /* Wait for all work on the simulation's stream. */
 int sbp_sync(sbp_sim *s);
+
+/* Checkpoint / resume (no counterpart in the paper).  The state of a
+ * simulation -- its six stored fields (raw storage values of the padded
+ * arrays), step index, probe samples and energy series -- as one host blob.
+ * sbp_checkpoint_bytes gives its size; sbp_save writes it to `host` (>= that
+ * many bytes; synchronises the stream; SBP_ECAPACITY if too small).  sbp_load
+ * restores it into a simulation created from the same descriptor, with the
+ * same sources and probes added (SBP_EINVAL if shape, precision or probe count
+ * differ); stepping on from there gives bit-identical results to stepping on
+ * from the saved simulation. */
+size_t sbp_checkpoint_bytes(const sbp_sim *s);
+int sbp_save(sbp_sim *s, void *host, size_t bytes);
+int sbp_load(sbp_sim *s, const void *host, size_t bytes);
 
 double sbp_dt(const sbp_sim *s);           /* time step in seconds            */
 int64_t sbp_step_index(const sbp_sim *s);  /* steps taken since creation      */

@@ -74,6 +74,8 @@ struct FusedParamsT {
     long long probe_cap, probe_slot, step;
     int kchunk;
     int *error_flag;                     // set to 1 when a pipeline wait gives up
+    unsigned wait_limit;                 // polls before a pipeline wait gives up
+    int test_stall;                      // test hook: issue no plane loads, so every wait runs out
 };
 using FusedParams = FusedParamsT<float>;
 
@@ -100,10 +102,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
         : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the phase did not complete within kWaitLimit polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity)
+// Bounded wait: false if the phase did not complete within `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned limit = kWaitLimit)
 {
-    for (unsigned it = 0; it < kWaitLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if (it > 64) __nanosleep(64);
     }
@@ -170,7 +172,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     }
     __syncthreads();
     int issued = 0;                                   // planes issued (thread 0's count)
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0 && !p.test_stall)
         for (; issued < kStages && issued < nplanes; ++issued)
             issue_plane<S>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
 
@@ -209,7 +211,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     // register carries of the previous plane (own columns): E^n, H^{n+1/2} and
     // the eps cells (rows j, j+1; columns i, i+1) of that plane
     float ec[2][3], hc[2][3], epc[2][3];
-    if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0); waited = 1; }
+    if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0, p.wait_limit); waited = 1; }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int re = (w + 1) * kBX + cx0 + lane + 32 * h;
@@ -227,7 +229,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     for (int q = k0; q <= k1 && !aborted; ++q) {
         const int iq = q - k0 + 1;                   // load index of plane q
         const int sq = iq % kStages;
-        if (ok) ok = mbar_wait_bounded(&bar[sq], (iq / kStages) & 1);
+        if (ok) ok = mbar_wait_bounded(&bar[sq], (iq / kStages) & 1, p.wait_limit);
         waited = iq + 1;
         const S *E0 = slotE(sq, 0), *E1 = slotE(sq, 1), *E2 = slotE(sq, 2);   // plane q
         const S *H0 = slotH(sq, 0), *H1 = slotH(sq, 1), *H2 = slotH(sq, 2);
@@ -352,7 +354,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         // still in flight so that none lands in shared memory after exit
         atomicExch(p.error_flag, 1);
         for (int L = waited > 0 ? waited - 1 : 0; L < issued; ++L)
-            (void)mbar_wait_bounded(&bar[L % kStages], (L / kStages) & 1);
+            (void)mbar_wait_bounded(&bar[L % kStages], (L / kStages) & 1, p.wait_limit);
     }
 }
 

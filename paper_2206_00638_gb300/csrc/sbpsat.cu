@@ -124,7 +124,7 @@ bool desc_valid(const sbp_grid_desc *d)
     for (int f = 0; f < 6; f++)
         if (d->face[f] < SBP_PEC || d->face[f] > SBP_INTERFACE) return false;
     if (d->energy_every < 0) return false;
-    if (d->flags & ~(SBP_FLAG_ALLOW_UNSTABLE | SBP_FLAG_FDTD)) return false;
+    if (d->flags & ~(SBP_FLAG_ALLOW_UNSTABLE | SBP_FLAG_FDTD | SBP_FLAG_TEST_WAIT_TIMEOUT)) return false;
     if (d->flags & SBP_FLAG_FDTD) {
         for (int f = 0; f < 6; f++)
             if (d->face[f] != SBP_PEC) return false;
@@ -144,10 +144,45 @@ bool desc_valid(const sbp_grid_desc *d)
 // z-block depths chosen by sbp_autotune, per grid shape and precision
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, int> g_tuned_depth;
+bool g_tune_file_read = false;
+
+// Optional persistence: SBP_TUNE_CACHE names a file of JSON lines
+// {"nx": .., "ny": .., "nz": .., "precision": .., "depth": ..}, read once and
+// appended to by every tuning.  Caller holds g_tune_mu.
+void read_tune_file()
+{
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *path = std::getenv("SBP_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[256];
+    while (std::fgets(line, sizeof(line), f)) {
+        int nx, ny, nz, prec, depth;
+        if (std::sscanf(line, " {\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d}", &nx, &ny,
+                        &nz, &prec, &depth) == 5 &&
+            depth > 0)
+            g_tuned_depth[std::make_tuple(nx, ny, nz, prec)] = depth;
+    }
+    std::fclose(f);
+}
+
+void append_tune_file(int nx, int ny, int nz, int prec, int depth)
+{
+    const char *path = std::getenv("SBP_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d}\n", nx, ny, nz, prec,
+                 depth);
+    std::fclose(f);
+}
 
 int tuned_depth(const sbp_grid_desc *d)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    read_tune_file();
     auto it = g_tuned_depth.find(std::make_tuple(d->nx, d->ny, d->nz, d->precision));
     return it == g_tuned_depth.end() ? 0 : it->second;
 }
@@ -518,6 +553,8 @@ int make_fused_params(const sbp_sim *s, int old, sbp::FusedParamsT<S> &fp)
     fp.step = p.step;
     fp.kchunk = s->fused_kchunk;
     fp.error_flag = s->error_flag;
+    fp.test_stall = (s->flags & SBP_FLAG_TEST_WAIT_TIMEOUT) ? 1 : 0;
+    fp.wait_limit = fp.test_stall ? (1u << 10) : sbp::kWaitLimit;
     return SBP_OK;
 }
 
@@ -948,7 +985,9 @@ int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
     if ((rc = check_error_flag(s))) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
+        read_tune_file();
         g_tuned_depth[std::make_tuple(s->n[0], s->n[1], s->n[2], s->prec)] = best;
+        append_tune_file(s->n[0], s->n[1], s->n[2], s->prec, best);
     }
     if (chosen) *chosen = best;
     if (best_ms) *best_ms = best_t;
@@ -1418,6 +1457,91 @@ int sbp_sync(sbp_sim *s)
     cudaSetDevice(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
     return check_error_flag(s);
+}
+
+// Checkpoint blob: header, the six stored fields of the current set (whole
+// padded arrays, raw storage values), the probe samples, the energy series.
+struct CkptHeader {
+    char magic[8];
+    int32_t version, precision;
+    int32_t n[3], nprobes;
+    int64_t step, probe_base, probe_cap, eseries_count;
+    uint64_t field_elems, esize, psize;
+};
+constexpr char kCkptMagic[8] = {'S', 'B', 'P', 'C', 'K', 'P', 'T', '1'};
+
+size_t ckpt_bytes(const sbp_sim *s)
+{
+    const size_t np = s->probe_buf ? s->prb.size() : 0;
+    return sizeof(CkptHeader) + 6 * s->field_elems * s->esize + np * (size_t)s->probe_cap * s->psize +
+           (size_t)s->eseries_count * sizeof(double);
+}
+
+size_t sbp_checkpoint_bytes(const sbp_sim *s) { return s ? ckpt_bytes(s) : 0; }
+
+int sbp_save(sbp_sim *s, void *host, size_t bytes)
+{
+    if (!s || !host) return SBP_EINVAL;
+    if (bytes < ckpt_bytes(s)) return SBP_ECAPACITY;
+    cudaSetDevice(s->device);
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    int rc = check_error_flag(s);
+    if (rc) return rc;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.precision = s->prec;
+    for (int a = 0; a < 3; a++) h.n[a] = s->n[a];
+    h.nprobes = s->probe_buf ? (int32_t)s->prb.size() : 0;
+    h.step = s->step;
+    h.probe_base = s->probe_base;
+    h.probe_cap = s->probe_buf ? s->probe_cap : 0;
+    h.eseries_count = s->eseries_count;
+    h.field_elems = s->field_elems;
+    h.esize = s->esize;
+    h.psize = s->psize;
+    char *p = static_cast<char *>(host);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const size_t fb = s->field_elems * s->esize;
+    for (int c = 0; c < 6; c++, p += fb) SBP_CUDA(cudaMemcpy(p, s->set[s->cur][c], fb, cudaMemcpyDeviceToHost));
+    const size_t pb = (size_t)h.nprobes * (size_t)h.probe_cap * s->psize;
+    if (pb) { SBP_CUDA(cudaMemcpy(p, s->probe_buf, pb, cudaMemcpyDeviceToHost)); p += pb; }
+    if (h.eseries_count)
+        SBP_CUDA(cudaMemcpy(p, s->eseries, h.eseries_count * sizeof(double), cudaMemcpyDeviceToHost));
+    return SBP_OK;
+}
+
+int sbp_load(sbp_sim *s, const void *host, size_t bytes)
+{
+    if (!s || !host || bytes < sizeof(CkptHeader)) return SBP_EINVAL;
+    CkptHeader h;
+    std::memcpy(&h, host, sizeof(h));
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1 || h.precision != s->prec ||
+        h.field_elems != s->field_elems || h.esize != s->esize || h.psize != s->psize)
+        return SBP_EINVAL;
+    for (int a = 0; a < 3; a++)
+        if (h.n[a] != s->n[a]) return SBP_EINVAL;
+    if (h.nprobes != 0 && h.nprobes != (int32_t)s->prb.size()) return SBP_EINVAL;
+    const size_t fb = s->field_elems * s->esize;
+    const size_t pb = (size_t)h.nprobes * (size_t)h.probe_cap * s->psize;
+    if (bytes < sizeof(h) + 6 * fb + pb + (size_t)h.eseries_count * sizeof(double)) return SBP_ECAPACITY;
+    cudaSetDevice(s->device);
+    int rc;
+    if (h.nprobes && (!s->probe_buf || s->probe_cap != h.probe_cap)) {
+        if ((rc = sbp_reserve_probes(s, h.probe_cap))) return rc;
+    }
+    if (h.eseries_count && (rc = ensure_series(s, h.eseries_count))) return rc;
+    SBP_CUDA(cudaStreamSynchronize(s->stream));
+    const char *p = static_cast<const char *>(host) + sizeof(h);
+    for (int c = 0; c < 6; c++, p += fb) SBP_CUDA(cudaMemcpy(s->set[s->cur][c], p, fb, cudaMemcpyHostToDevice));
+    if (pb) { SBP_CUDA(cudaMemcpy(s->probe_buf, p, pb, cudaMemcpyHostToDevice)); p += pb; }
+    if (h.eseries_count) SBP_CUDA(cudaMemcpy(s->eseries, p, h.eseries_count * sizeof(double), cudaMemcpyHostToDevice));
+    s->step = h.step;
+    s->probe_base = h.probe_base;
+    s->eseries_count = h.eseries_count;
+    return SBP_OK;
 }
 
 double sbp_dt(const sbp_sim *s) { return s ? s->dt : 0.0; }

@@ -33,6 +33,7 @@ EX, EY, EZ, HX, HY, HZ = range(6)
 GAUSS, GAUSS_DERIV, MOD_GAUSS = 0, 1, 2
 FLAG_ALLOW_UNSTABLE = 1
 FLAG_FDTD = 2          # plain Yee FDTD comparator (six PEC faces, one-pass path)
+FLAG_TEST_WAIT_TIMEOUT = 4   # test hook: the one-pass pipeline waits run out (SBP_ETIMEOUT)
 
 ON_PLUS = ((0, 1, 1), (1, 0, 1), (1, 1, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))
 
@@ -107,6 +108,9 @@ def lib():
                 "sbp_half_step_e": (I, [pp, I]),
                 "sbp_autotune": (I, [P, I, C.POINTER(C.c_int), C.POINTER(D)]),
                 "sbp_connect_phase": (I, [P, P, I, D]),
+                "sbp_checkpoint_bytes": (SZ, [P]),
+                "sbp_save": (I, [P, P, SZ]),
+                "sbp_load": (I, [P, P, SZ]),
                 "sbp_step_timed": (I, [P, I64, C.POINTER(C.c_double), C.POINTER(C.c_int64), I]),
                 "sbp_get_probes": (I, [P, C.POINTER(C.c_double), I64, C.POINTER(C.c_int64)]),
                 "sbp_energy": (I, [P, C.POINTER(C.c_double)]),
@@ -138,7 +142,7 @@ def exported_symbols() -> Sequence[str]:
     return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_connect_phase", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
             "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_autotune", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
-            "sbp_sync", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
+            "sbp_sync", "sbp_checkpoint_bytes", "sbp_save", "sbp_load", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
             "sbp_batch_create", "sbp_batch_add", "sbp_batch_remove", "sbp_batch_remaining", "sbp_batch_step",
             "sbp_batch_size", "sbp_batch_destroy", "sbp_server_create", "sbp_server_submit", "sbp_server_poll",
             "sbp_server_probes", "sbp_server_release", "sbp_server_drain", "sbp_server_stats", "sbp_server_destroy"]
@@ -304,6 +308,19 @@ class Sim:
         depth, ms = C.c_int(), C.c_double()
         _check(lib().sbp_autotune(self._h, int(trial_steps), C.byref(depth), C.byref(ms)), "sbp_autotune")
         return depth.value, ms.value
+
+    def save(self) -> bytes:
+        """Checkpoint: the simulation's state as bytes (sbp_save)."""
+        n = lib().sbp_checkpoint_bytes(self._h)
+        buf = C.create_string_buffer(n)
+        _check(lib().sbp_save(self._h, buf, n), "sbp_save")
+        return buf.raw
+
+    def load(self, blob: bytes):
+        """Restore a checkpoint written by ``save`` of a simulation with the same
+        descriptor, sources and probes (sbp_load)."""
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib().sbp_load(self._h, buf, len(blob)), "sbp_load")
 
     def sync(self):
         _check(lib().sbp_sync(self._h), "sbp_sync")
