@@ -30,6 +30,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sbpsat.h"
 #include "kernels.cuh"
 #include "fused.cuh"
@@ -41,6 +43,13 @@ constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kMu0 = 1.25663706212e-6;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// NVTX range for the duration of a scope (visible in a profiler's timeline;
+// a no-op when no tool is attached).
+struct Trace {
+    explicit Trace(const char *name) { nvtxRangePushA(name); }
+    ~Trace() { nvtxRangePop(); }
+};
 
 }  // namespace
 
@@ -814,6 +823,7 @@ int half_e(sbp_sim **sims, int nsims)
 
 int step_group(sbp_sim **sims, int nsims, int64_t nsteps)
 {
+    Trace trace("sbp_step");
     if (nsteps < 0) return SBP_EINVAL;
     int rc = check_group(sims, nsims);
     if (rc) return rc;
@@ -956,6 +966,7 @@ int time_trials(sbp_sim *s, int trials, cudaEvent_t e0, cudaEvent_t e1, float *m
 
 int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
 {
+    Trace trace("sbp_autotune");
     if (!s->fused_ok || linked_to_other(s)) return SBP_ESTATE;
     const int span = s->n[2] - 5;                      // interior E planes of the one-pass step
     std::vector<int> cand;
@@ -1393,6 +1404,7 @@ int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples)
 
 int sbp_energy_group(sbp_sim **sims, int nsims, double *W)
 {
+    Trace trace("sbp_energy");
     if (!sims || nsims <= 0 || !W) return SBP_EINVAL;
     double total = 0.0;
     for (int q = 0; q < nsims; q++) {
@@ -1481,6 +1493,7 @@ size_t sbp_checkpoint_bytes(const sbp_sim *s) { return s ? ckpt_bytes(s) : 0; }
 
 int sbp_save(sbp_sim *s, void *host, size_t bytes)
 {
+    Trace trace("sbp_save");
     if (!s || !host) return SBP_EINVAL;
     if (bytes < ckpt_bytes(s)) return SBP_ECAPACITY;
     cudaSetDevice(s->device);
@@ -1515,6 +1528,7 @@ int sbp_save(sbp_sim *s, void *host, size_t bytes)
 
 int sbp_load(sbp_sim *s, const void *host, size_t bytes)
 {
+    Trace trace("sbp_load");
     if (!s || !host || bytes < sizeof(CkptHeader)) return SBP_EINVAL;
     CkptHeader h;
     std::memcpy(&h, host, sizeof(h));
@@ -1632,6 +1646,7 @@ int sbp_batch_remaining(const sbp_batch *b, const sbp_sim *s, int64_t *remaining
 
 int sbp_batch_step(sbp_batch *b, int64_t nsteps)
 {
+    Trace trace("sbp_batch_step");
     if (!b || nsteps < 0) return SBP_EINVAL;
     cudaSetDevice(b->device);
     if (b->m.empty() || nsteps == 0) return SBP_OK;

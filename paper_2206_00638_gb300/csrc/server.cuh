@@ -97,6 +97,7 @@ void finish(sbp_server *S, const std::shared_ptr<ServerRequest> &r, int status)
 // stream, which waits for the set-up to finish before the next chunk.
 int admit(sbp_server *S, const std::shared_ptr<ServerRequest> &r)
 {
+    Trace trace("sbp_server_admit");
     cudaError_t e = cudaMallocAsync(&r->ws, r->ws_bytes, S->adm);
     if (e != cudaSuccess) { (void)cudaGetLastError(); r->ws = nullptr; return cuda_fail(e); }
     sbp_sim *s = nullptr;
