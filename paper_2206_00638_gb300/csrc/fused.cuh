@@ -644,7 +644,7 @@ __device__ __forceinline__ void band_e_warp(const Params<T, S> &p, const Band &b
 }
 
 template <typename T, bool MUVAR, typename S>
-__global__ void __launch_bounds__(256) band_e(const Params<T, S> p, const Band b, S *ex_out, S *ey_out, S *ez_out)
+__global__ void __launch_bounds__(256, 4) band_e(const Params<T, S> p, const Band b, S *ex_out, S *ey_out, S *ez_out)
 {
     const unsigned w = blockIdx.x * 8u + (threadIdx.x >> 5);
     if (w >= b.wz + b.wy + b.wx) return;
