@@ -175,6 +175,16 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     if (threadIdx.x == 0 && !p.test_stall)
         for (; issued < kStages && issued < nplanes; ++issued)
             issue_plane<S>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
+    // J(t^{n+1/2}) of every source is the same at each node it reaches, so
+    // warp 1 evaluates it once per CTA (FP64 waveform, rounded to FP32 once)
+    // while the first planes load; it is first read after the barrier below.
+    static_assert(kMaxSources <= 32, "one lane of warp 1 per source");
+    __shared__ float sJ[kMaxSources];
+    if (SRC && w == 1 && lane < p.nsrc) {
+        const Src &Sr = p.src[lane];
+        const double t_half = ((double)step + 0.5) * p.dt;
+        sJ[lane] = (float)(Sr.amp * waveform(Sr.wf, t_half, Sr.tw, Sr.t0, Sr.f));
+    }
 
     // per-thread probe / source masks for the two columns
     unsigned long long pmask[2] = {0ull, 0ull};
@@ -203,7 +213,6 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     }
     const Coef<float> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
     const Coef<float> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
-    const double t_half = ((double)step + 0.5) * p.dt;
 
     bool ok = true;
     bool aborted = false;
@@ -238,6 +247,12 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         const float *Hp = hbuf + ((q - 1) & 1) * (3 * kFTY * kFTX);
         const bool doE = q > k0;
         const int pl = q - 1;
+        // sources acting on E plane pl, looked up only by threads whose
+        // columns some source reaches
+        unsigned splane = 0u;
+        if (SRC && (smask[0] | smask[1]))
+            for (int b = 0; b < p.nsrc; ++b)
+                if (p.src[b].k < 0 || p.src[b].k == pl) splane |= 1u << b;
 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -301,18 +316,16 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                 const float sx = epc[h][0] + qa;
                 const float sy = epc[h][1] + qb;
                 const float sz = epc[h][1] + epc[h][2];
-                if (SRC && smask[h]) {
-                    unsigned m = smask[h];
+                if (SRC && (smask[h] & splane)) {
+                    unsigned m = smask[h] & splane;
                     while (m) {
                         const int b = __ffs(m) - 1;
                         m &= m - 1;
-                        const Src &Sr = p.src[b];
-                        if (Sr.k < 0 || Sr.k == pl) {
-                            const float J = (float)(Sr.amp * waveform(Sr.wf, t_half, Sr.tw, Sr.t0, Sr.f));
-                            if (Sr.comp == 0) ax.add(p.AJ, J, -1.f);
-                            else if (Sr.comp == 1) ay.add(p.AJ, J, -1.f);
-                            else az.add(p.AJ, J, -1.f);
-                        }
+                        const float J = sJ[b];
+                        const int comp = p.src[b].comp;
+                        if (comp == 0) ax.add(p.AJ, J, -1.f);
+                        else if (comp == 1) ay.add(p.AJ, J, -1.f);
+                        else az.add(p.AJ, J, -1.f);
                     }
                 }
                 const float ex = quant<S>(ec[h][0] + scaled_increment(ax, sx));
