@@ -182,12 +182,47 @@ def test_fp32_accuracy_2000_steps():
 
 
 def test_full_size_dielectric_256():
-    """Full-size 256^3 dielectric workload in the benchmark's launch configuration:
-    element-wise parity for the first 40 steps (every field), FP32."""
+    """Full-size 256^3 dielectric workload in the benchmark's launch configuration (the
+    z-block depth the autotuner picks, as bench.py does before timing): element-wise parity
+    for the first 40 steps (every field), FP32."""
     w = wl.dielectric(N=256, steps=40)
-    errs, perr = _run_and_compare(w, w.steps, sbpsat.FP32)
+    sim = sbpsat.from_workload(w, precision=sbpsat.FP32)[0]
+    depth, _ = sim.autotune(3)
+    assert depth > 0
+    sim.reserve_probes(w.steps)
+    sim.step(w.steps)
+    blocks = parity.oracle_run(w, w.steps, sim.dt)
+    errs = parity.compare([sim], blocks)
+    perr = parity.probe_error([sim], blocks)
+    sim.close()
     assert max(errs[0]) < 1e-5, errs
     assert perr < 1e-4
+
+
+@pytest.mark.parametrize("precision", [sbpsat.FP32, sbpsat.FP32_FP16STORE])
+def test_full_size_512_mixed_one_pass_equals_in_place(precision, monkeypatch):
+    """The largest configuration, 512^3 with PMC / PEC / absorbing face pairs, four
+    dielectric spheres and a sheet source, at full size: the one-pass + band path and the
+    in-place half-step path (two separate kernel sets, the latter checked against the oracle
+    at every small size above) agree bit for bit after 20 steps, fields and probes.  The
+    oracle itself cannot run this size; its parity for this workload is the 128^3 copy."""
+    w = wl.mixed_faces(N=512, steps=20)
+    fused = parity.gpu_run(w, 20, precision)[0]
+    monkeypatch.setenv("SBP_NO_FUSED", "1")
+    plain = parity.gpu_run(w, 20, precision)[0]
+    for c in range(6):
+        a = torch.empty(fused.shape(c), dtype=torch.float32, device="cuda")
+        b = torch.empty(plain.shape(c), dtype=torch.float32, device="cuda")
+        fused.field(c, out=a)
+        plain.field(c, out=b)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b), c
+        if c == 1:
+            assert torch.count_nonzero(a).item() > 0        # the sheet has driven E_y
+        del a, b
+    assert np.array_equal(fused.probes(), plain.probes())
+    fused.close()
+    plain.close()
 
 
 @pytest.mark.parametrize("n", [(70, 43, 37), (130, 20, 17), (8, 8, 8), (9, 13, 10)])
