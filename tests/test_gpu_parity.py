@@ -159,6 +159,51 @@ def test_deterministic_and_own_memory():
     assert np.array_equal(s1.probes(), s2.probes())
 
 
+def test_bitwise_reproducible_under_concurrent_load():
+    """The one-pass step, band H and band E run concurrently on two streams; their node sets
+    overlap only on the first interior layer, written with the same bits.  So a run gives the
+    same bits however the kernels interleave: alone, and with an unrelated workload keeping
+    the GPU busy on another stream (64^3 dielectric cube, 600 steps, fields and probes)."""
+    import threading
+
+    w = wl.dielectric(N=64, steps=600)
+
+    def run(load):
+        sim = sbpsat.from_workload(w, precision=sbpsat.FP32)[0]
+        sim.reserve_probes(w.steps)
+        stop = [False]
+        th = None
+        if load:
+            st = torch.cuda.Stream()
+            x = torch.rand(1 << 24, device="cuda")
+
+            def busy():
+                with torch.cuda.stream(st):
+                    while not stop[0]:
+                        for _ in range(20):
+                            x.mul_(1.0000001).add_(1e-9)
+                        st.synchronize()
+
+            th = threading.Thread(target=busy)
+            th.start()
+        try:
+            for _ in range(6):
+                sim.step(100)
+            out = [sim.field(c) for c in range(6)] + [sim.probes()]
+        finally:
+            stop[0] = True
+            if th is not None:
+                th.join()
+        sim.close()
+        return out
+
+    ref = run(False)
+    for load in (True, False, True):
+        got = run(load)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+
+
 def test_device_field_roundtrip():
     w = wl.random_box((12, 10, 9), seed=1, sources=False)
     sim = sbpsat.from_workload(w)[0]
