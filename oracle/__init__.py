@@ -10,8 +10,9 @@ Every function of the C file cites the passage it follows.  Pins (tests under
 ``tests/test_oracle_*.py``) tie it to the paper's exact SBP identities, to the
 Kronecker construction of Eqs. (ED_1)-(ED_3) built from the printed Q
 matrices, to energy conservation, to the analytic cavity resonance and to a
-1D reduction.  Parity unpinned: the absolute accuracy of the absorbing and
-interface penalties beyond their energy sign and 1D reflection tests.
+1D reduction.  The absorbing penalty (not the paper's) is pinned to the
+closed-form oblique reflection of the first-order characteristic condition;
+the interface penalty to the printed periodic-SAT matrices (1D complex pair).
 """
 from __future__ import annotations
 
