@@ -274,3 +274,61 @@ def test_absorbing_oblique_reflection_closed_form(theta):
     c = math.cos(math.radians(theta))
     expect = (1 - c) / (1 + c)
     assert abs(r_abs / r_pec - expect) < 0.1 * expect, (r_abs, r_pec, expect)
+
+
+def _fresnel_normal(two_blocks, er2=4.0, ppw=20, w_wl=3.0):
+    """Reflected and transmitted E envelope, relative to the incident one, of a plane-wave packet
+    (E_x, fields uniform in x and y through zero-phase periodic x and y faces) crossing from
+    eps_r = 1 into eps_r = er2 at normal incidence: one block whose cells change at the plane
+    (node material = closed-box cell mean), or two blocks joined there by the interface SAT.
+    Absorbing z faces far from the packet; E^0 only, so half of the packet travels up."""
+    h = 1e-3
+    lam = ppw * math.sqrt(er2) * h                # ppw points per wavelength in the dense medium
+    w = w_wl * lam
+    gap = int(round(2.5 * w / h))
+    k0 = gap + 10                                 # packet; probe at k0 + gap; step at k0 + 2 gap
+    ki = k0 + 2 * gap
+    nz = ki + 2 * gap
+    dt = oracle.dt_cfl(0.95, h, h, h)
+    if not two_blocks:
+        eps = np.ones((nz, 4, 4))
+        eps[ki:] = er2
+        lo = hi = oracle.Block((4, 4, nz), (h,) * 3, dt, (PEC, PEC, PEC, PEC, ABSORBING, ABSORBING), eps_r=eps)
+        blocks, k_hi = [lo], ki + gap
+    else:
+        lo = oracle.Block((4, 4, ki), (h,) * 3, dt, (PEC, PEC, PEC, PEC, ABSORBING, PEC))
+        hi = oracle.Block((4, 4, nz - ki), (h,) * 3, dt, (PEC, PEC, PEC, PEC, PEC, ABSORBING),
+                          eps_r=np.full((nz - ki, 4, 4), er2))
+        oracle.connect(lo, 5, hi, 4)
+        blocks, k_hi = [lo, hi], gap
+    for b in blocks:
+        oracle.connect(b, 0, b, 1)
+        oracle.connect(b, 2, b, 3)
+    shp = lo.shape(EX)
+    z = np.arange(shp[0]) * h
+    env = np.exp(-((z - k0 * h) / w) ** 2) * np.cos(2 * math.pi / lam * (z - k0 * h))
+    lo.set_field(EX, np.ascontiguousarray(env[:, None, None] * np.ones(shp)))
+    lo.add_probe(EX, 1, 1, k0 + gap)
+    hi.add_probe(EX, 1, 1, k_hi)
+    v = 299792458.0 * dt
+    steps = int(4.0 * gap * h / v)
+    for b in blocks:
+        b.reserve_probes(steps)
+    oracle.step(blocks, steps)
+    below, above = lo.probes()[0], hi.probes()[-1]
+    mid = int(2 * gap * h / v)
+    inc = np.abs(below[:mid]).max()
+    return np.abs(below[mid:]).max() / inc, np.abs(above).max() / inc
+
+
+@pytest.mark.parametrize("two_blocks", [False, True])
+def test_dielectric_step_fresnel(two_blocks):
+    """A dielectric step eps_r 1 -> 4 reflects and transmits a normally incident wave with the
+    Fresnel coefficients |R| = (n2 - n1)/(n1 + n2) = 1/3 and T = 2 n1/(n1 + n2) = 2/3 (for E):
+    inside one block (node material, reading 4) and across two blocks joined by the interface
+    SAT.  At 20 points per wavelength in the dense medium: R within 0.03 and T within 0.06
+    (measured 0.328-0.330 and 0.641; 0.332-0.333 and 0.663 at 40 points).  An interface
+    coefficient of 3/4 instead of 1/2 (a planted mistake, not committed) goes unstable."""
+    R, T = _fresnel_normal(two_blocks)
+    assert abs(R - 1.0 / 3.0) < 0.03, R
+    assert abs(T - 2.0 / 3.0) < 0.06, T
