@@ -111,6 +111,18 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity
     }
     return false;
 }
+// Orders this thread's earlier shared-memory reads (generic proxy) before the
+// TMA copies (async proxy) that the next CTA barrier releases into the stage
+// they read.  A warp passes a barrier with a load still outstanding when the
+// value is first used after the barrier; the copy could then overwrite the
+// slot before the load reads it.  Within a block that happens only to the
+// carries read before the plane loop (E of plane k0-1) and to the eps cells
+// of its first plane (no E update yet): every other value read from a stage
+// feeds a store issued before that plane's barrier.
+__device__ __forceinline__ void fence_generic_to_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
     asm volatile(
@@ -229,6 +241,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
 #pragma unroll
         for (int f = 0; f < 3; ++f) epc[h][f] = 0.f;
     }
+    fence_generic_to_async();                         // the E carries of plane k0-1
     if (__syncthreads_or(!ok)) aborted = true;
     if (!aborted && threadIdx.x == 0 && kStages < nplanes) {   // plane k0-1 is in registers now
         issue_plane<S>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
@@ -353,6 +366,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             epc[h][0] = qa; epc[h][1] = qb; epc[h][2] = qc;
         }
         // one barrier per plane: hbuf[q&1] complete, hbuf[(q-1)&1] and stage q free
+        if (!doE) fence_generic_to_async();           // the eps carries of plane k0
         if (__syncthreads_or(!ok)) { aborted = true; break; }
         if (threadIdx.x == 0) {
             const int nxt = q + kStages;
