@@ -12,7 +12,10 @@ Kronecker construction of Eqs. (ED_1)-(ED_3) built from the printed Q
 matrices, to energy conservation, to the analytic cavity resonance and to a
 1D reduction.  The absorbing penalty (not the paper's) is pinned to the
 closed-form oblique reflection of the first-order characteristic condition;
-the interface penalty to the printed periodic-SAT matrices (1D complex pair).
+the interface penalty to the printed periodic-SAT matrices (1D complex pair)
+and to the Fresnel coefficients of a dielectric step.  The current sources are
+pinned to the field a current sheet radiates (-eta K / 2) and to the full
+Hertzian-dipole field of a point current element.
 """
 from __future__ import annotations
 
