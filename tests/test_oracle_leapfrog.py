@@ -410,3 +410,63 @@ def test_point_current_radiates_hertzian_dipole_field():
         before_echo = t < (2 * (n - c) - d) * h / _C0     # first echo: off the x+ face
         err = np.abs(b.probes()[q][before_echo] - expect[before_echo]).max() / np.abs(expect).max()
         assert err < 0.05, (d, err)
+
+
+def _grid_nodes(n, h, plus):
+    """Node positions of the plus grid x_i = i h or of the minus grid
+    [x_0, x_{1/2}, ..., x_{n-1/2}, x_n] (Sec. II, the two one-dimensional grids)."""
+    if plus:
+        return np.arange(n + 1) * h
+    return np.concatenate([[0.0], (np.arange(1, n + 1) - 0.5) * h, [n * h]])
+
+
+# E_x .. H_z = prod over axes of cos(k pi x / L + phase): (k, phase) per component and axis
+_ENERGY_MODES = [[(1.3, 0.4), (0.7, 1.1), (2.1, 0.2)], [(0.9, 0.3), (1.7, 0.5), (0.6, 1.3)],
+                 [(1.1, 0.8), (0.5, 0.1), (1.9, 0.6)], [(2.3, 0.2), (1.2, 0.9), (0.8, 0.4)],
+                 [(0.6, 1.0), (2.0, 0.3), (1.4, 0.7)], [(1.5, 0.6), (0.9, 1.2), (1.0, 0.5)]]
+
+
+def _energy_rel_error(m, er=2.5, mr=1.5):
+    """(W - exact) / exact of the E part (H = 0) and of the H part (E = 0) of the oracle's
+    energy for smooth fields on a 0.9 x 0.7 x 0.5 m box of 9m x 8m x 6m cells."""
+    L = (0.9, 0.7, 0.5)
+    n = (9 * m, 8 * m, 6 * m)
+    h = tuple(L[a] / n[a] for a in range(3))
+    on_plus = ((0, 1, 1), (1, 0, 1), (1, 1, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))   # Table I
+    xg, wg = np.polynomial.legendre.leggauss(200)
+
+    def mode(c, a, x):
+        k, ph = _ENERGY_MODES[c][a]
+        return np.cos(k * math.pi * x / L[a] + ph)
+
+    out = []
+    for comps, coef in ((range(3), _EPS0 * er), (range(3, 6), _MU0 * mr)):
+        b = oracle.Block(n, h, oracle.dt_cfl(0.5, *h), (PEC,) * 6, eps_r=np.full(n[::-1], er),
+                         mu_r=np.full(n[::-1], mr))
+        exact = 0.0
+        for c in comps:
+            x, y, z = (_grid_nodes(n[a], h[a], on_plus[c][a]) for a in range(3))
+            f = mode(c, 2, z)[:, None, None] * mode(c, 1, y)[None, :, None] * mode(c, 0, x)[None, None, :]
+            assert f.shape == tuple(b.shape(c))
+            b.set_field(c, np.ascontiguousarray(f))
+            term = 1.0
+            for a in range(3):                     # Gauss-Legendre on [0, L_a], exact here
+                xa = 0.5 * L[a] * (xg + 1)
+                term *= np.sum(0.5 * L[a] * wg * mode(c, a, xa) ** 2)
+            exact += term
+        exact *= 0.5 * coef
+        out.append((oracle.energy([b]) - exact) / exact)
+    return out
+
+
+def test_energy_converges_to_field_energy():
+    """The discrete energy of Eq. (16) (E^T eps P E + H^{n-1/2} mu P H^{n+1/2}, halved) of
+    smooth fields converges to the continuous (1/2) int eps E^2 + mu H^2 dV at second order:
+    within 2.5e-3 on 9x8x6 x 4 cells and 5e-4 at twice the resolution (measured 1.2e-3 / 7e-4
+    and 2.2e-4 / 2.3e-4), on a box with three different spacings, eps_r 2.5 and mu_r 1.5.
+    Each field sits on its own grid pair (Table I) and takes that pair's norm weights.
+    Uniform weights (closure weights dropped), the spacing of the wrong axis or a missing
+    material factor (planted mistakes, not committed) fail it."""
+    coarse, fine = _energy_rel_error(4), _energy_rel_error(8)
+    assert max(abs(v) for v in coarse) < 2.5e-3, coarse
+    assert max(abs(v) for v in fine) < 5e-4, fine
