@@ -470,3 +470,35 @@ def test_energy_converges_to_field_energy():
     coarse, fine = _energy_rel_error(4), _energy_rel_error(8)
     assert max(abs(v) for v in coarse) < 2.5e-3, coarse
     assert max(abs(v) for v in fine) < 5e-4, fine
+
+
+@pytest.mark.parametrize("face, expect", [(PEC, -1.0), (PMC, 1.0)])
+def test_pec_pmc_reflection_sign(face, expect):
+    """At normal incidence a PEC wall reflects E with coefficient -1 (tangential E vanishes
+    there) and a PMC wall with +1 (tangential H vanishes, so E doubles).  A Gaussian E_x pulse of
+    12 cells with H = 0 splits into two halves of amplitude 1/2; the upward half is probed
+    before and after the z+ face: 1/2 within 0.5 %, ratio within 1 % (measured 0.08 % and
+    0.07 %, and 0.02 % at 20 cells)."""
+    h, wc = 1e-3, 12
+    gap = 4 * wc
+    k0 = gap + 10
+    nz = k0 + 2 * gap
+    dt = oracle.dt_cfl(0.95, h, h, h)
+    b = oracle.Block((4, 4, nz), (h,) * 3, dt, (PEC, PEC, PEC, PEC, ABSORBING, face))
+    oracle.connect(b, 0, b, 1)
+    oracle.connect(b, 2, b, 3)
+    shp = b.shape(EX)
+    z = np.arange(shp[0]) * h
+    pulse = np.exp(-((z - k0 * h) / (wc * h)) ** 2)
+    b.set_field(EX, np.ascontiguousarray(pulse[:, None, None] * np.ones(shp)))
+    b.add_probe(EX, 1, 1, k0 + gap)
+    v = 299792458.0 * dt
+    steps = int(3.0 * gap * h / v)
+    b.reserve_probes(steps)
+    oracle.step([b], steps)
+    p = b.probes()[0]
+    mid = int(2 * gap * h / v)                    # between the incident and reflected passes
+    inc = p[:mid][np.argmax(np.abs(p[:mid]))]
+    ref = p[mid:][np.argmax(np.abs(p[mid:]))]
+    assert abs(inc - 0.5) < 0.0025, inc
+    assert abs(ref / inc - expect) < 0.01, ref / inc
