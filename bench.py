@@ -120,6 +120,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.rows)}
 
 
+def max_over_ranks(ms, world, device):
+    """The job's time: the slowest rank's, by an all-reduce MAX when there are several."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells, steps, world, ms_max):
+    """Whole-job Gcell-updates/s: each of the `world` ranks advances its own replica of
+    `cells` cells by `steps` steps within `ms_max` milliseconds."""
+    return cells * steps * world / (ms_max * 1e-3) / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -200,12 +216,8 @@ def run_ours(args):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = start.elapsed_time(stop)
-    t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = cells * args.steps * world / (ms_max * 1e-3) / 1e9
+    ms_max = max_over_ranks(start.elapsed_time(stop), world, "cuda")
+    value = job_throughput(cells, args.steps, world, ms_max)
 
     # per-kernel durations: further steps with CUDA events around every launch
     nk = min(args.steps, 400)
