@@ -1,0 +1,148 @@
+"""Which kernel writes which node on the one-pass path, replayed on the CPU.
+
+A Python copy of the index arithmetic of the one-pass tiles (fused_interior: tile origin,
+column / row ownership, z-blocks), of the band geometry set up on the host, and of the band
+warps' node decoding (band_lane, with the per-component `have` masks).  Over grids near every
+tiling boundary, every node of every component must be written exactly once in each phase.
+The one exception is the first interior H layer (index 3 or n-2 on some axis, inside
+[3, n-2]^3), which the one-pass step and band H both write with the same bits.  A change to
+either side's indexing that loses or doubles a node fails here before any GPU run.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+FTX, FTY = 64, 8                        # H footprint of a one-pass CTA: columns x rows
+ON_PLUS = ((0, 1, 1), (1, 0, 1), (1, 1, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1))
+
+
+def extents(n, c):
+    """Nodes per axis of component c: n+1 on the plus grid, n+2 on the minus grid."""
+    return tuple(n[a] + (1 if ON_PLUS[c][a] else 2) for a in range(3))
+
+
+def fused_nodes(n, depth):
+    """(H nodes, E nodes) the one-pass kernel stores, as lists of (i, j, k) (one entry per store)."""
+    nx, ny, nz = n
+    tx = (nx - 5 + FTX - 2) // (FTX - 1)
+    ty = (ny - 5 + FTY - 2) // (FTY - 1)
+    tz = (nz - 5 + depth - 1) // depth
+    hs, es = [], []
+    for bx, by, bz in itertools.product(range(tx), range(ty), range(tz)):
+        x0, y0, k0 = 3 + bx * (FTX - 1), 3 + by * (FTY - 1), 3 + bz * depth
+        k1 = min(k0 + depth, nz - 2)
+        for w in range(FTY):
+            j = y0 + w
+            row_e = w < FTY - 1 and j <= ny - 3
+            row_h = j <= ny - 2 and (w < FTY - 1 or j == ny - 2)
+            for c in range(FTX):
+                i = x0 + c
+                col_h = row_h and i <= nx - 2 and (c < FTX - 1 or i == nx - 2)
+                col_e = row_e and c < FTX - 1 and i <= nx - 3
+                for q in range(k0, k1 + 1):
+                    if col_h and (q < k1 or q == nz - 2):
+                        hs.append((i, j, q))
+                    if q > k0 and col_e:
+                        es.append((i, j, q - 1))
+    return hs, es
+
+
+def band_geometry(n, lo):
+    hi = [n[a] - 3 for a in range(3)]
+    segs = hi[0] // 32 + 1
+    ey, ez = n[1] + 2, n[2] + 2
+    zplanes = lo + (n[2] + 1 - hi[2])
+    yrows = lo + (n[1] + 1 - hi[1])
+    jin = hi[1] - lo + 1
+    xgroups = (ey + 7) // 8
+    wz, wy, wx = zplanes * jin * segs, ez * yrows * segs, ez * xgroups * 2
+    return dict(lo=lo, hi=hi, segs=segs, jin=jin, yrows=yrows, xgroups=xgroups, wz=wz, wy=wy, wx=wx)
+
+
+def band_lane(b, n, w, lane):
+    """(i, j, k) of the lane's node in band warp w, or None."""
+    lo, hi = b["lo"], b["hi"]
+    if w < b["wz"] + b["wy"]:
+        zs = w < b["wz"]
+        if not zs:
+            w -= b["wz"]
+        r, seg = divmod(w, b["segs"])
+        if zs:
+            pl, jr = divmod(r, b["jin"])
+            j = lo + jr
+            k = pl if pl < lo else hi[2] + 1 + (pl - lo)
+        else:
+            k, jr = divmod(r, b["yrows"])
+            j = jr if jr < lo else hi[1] + 1 + (jr - lo)
+        i = seg * 32 + lane
+        return (i, j, k) if lo <= i <= hi[0] else None
+    w -= b["wz"] + b["wy"]
+    side, r = w & 1, w >> 1
+    k, g = divmod(r, b["xgroups"])
+    jl = 8 * g
+    jh = min(jl + 7, n[1] + 1)
+    j = jl + (lane >> 2)
+    c = lane & 3
+    i = (hi[0] + 1 if side else 0) + c
+    ok = j <= jh and (i <= n[0] + 1 if side else c < lo)
+    return (i, j, k) if ok else None
+
+
+def band_nodes(n, lo):
+    b = band_geometry(n, lo)
+    out = []
+    for w in range(b["wz"] + b["wy"] + b["wx"]):
+        for lane in range(32):
+            node = band_lane(b, n, w, lane)
+            if node is not None:
+                out.append(node)
+    return out
+
+
+def _counts(n, comps, written):
+    """Per component, how many times each node of its extent is written."""
+    res = {}
+    for c in comps:
+        ext = extents(n, c)
+        cnt = np.zeros(ext, dtype=np.int32)
+        for nodes in written:
+            for (i, j, k) in nodes:
+                if i < ext[0] and j < ext[1] and k < ext[2]:
+                    cnt[i, j, k] += 1
+        res[c] = cnt
+    return res
+
+
+GRIDS = [((8, 8, 8), 8), ((9, 12, 13), 8), ((10, 13, 21), 13), ((68, 12, 17), 8), ((69, 20, 9), 8),
+         ((70, 19, 33), 13), ((40, 11, 40), 64)]
+
+
+@pytest.mark.parametrize("n, depth", GRIDS)
+def test_every_node_written_once(n, depth):
+    fh, fe = fused_nodes(n, depth)
+    bh, be = band_nodes(n, 4), band_nodes(n, 3)
+    for nodes in (fh, fe, bh, be):                                  # no kernel writes a node twice
+        assert len(nodes) == len(set(nodes))
+    # H: once, except the first interior layer, written by both (same bits)
+    for c, cnt in _counts(n, range(3, 6), [fh, bh]).items():
+        idx = np.indices(cnt.shape)
+        inner = np.all([(idx[a] >= 3) & (idx[a] <= n[a] - 2) for a in range(3)], axis=0)
+        deep = np.all([(idx[a] >= 4) & (idx[a] <= n[a] - 3) for a in range(3)], axis=0)
+        layer = inner & ~deep
+        assert np.all(cnt[~layer] == 1), (c, np.argwhere(cnt[~layer] != 1)[:5])
+        assert np.all(cnt[layer] == 2), c
+    for c, cnt in _counts(n, range(3), [fe, be]).items():
+        assert np.all(cnt == 1), (c, np.argwhere(cnt != 1)[:5])
+    # the one-pass kernel stays inside its boxes
+    assert all(3 <= v[a] <= n[a] - 2 for v in fh for a in range(3))
+    assert all(3 <= v[a] <= n[a] - 3 for v in fe for a in range(3))
+
+
+def test_band_geometry_is_what_the_host_accepts():
+    """x-end slabs at most 4 nodes wide, and x segments from 0 reach past the interior."""
+    for n in (8, 13, 64, 255, 512):
+        for lo in (3, 4):
+            b = band_geometry((n, n, n), lo)
+            assert lo <= 4 and n + 1 - b["hi"][0] <= 4
+            assert b["segs"] * 32 > b["hi"][0]
