@@ -146,3 +146,37 @@ def test_band_geometry_is_what_the_host_accepts():
             b = band_geometry((n, n, n), lo)
             assert lo <= 4 and n + 1 - b["hi"][0] <= 4
             assert b["segs"] * 32 > b["hi"][0]
+
+
+def _find_slot(pre, n, b):
+    """The batched kernels' lookup: the largest g < n with pre[g] <= b (binary search)."""
+    lo, hi = 0, n - 1
+    while lo < hi:
+        mid = (lo + hi + 1) >> 1
+        if pre[mid] <= b:
+            lo = mid
+        else:
+            hi = mid - 1
+    return lo
+
+
+def test_batched_ctas_map_to_every_tile_of_every_grid_once():
+    """A batched launch of sum(count_g) CTAs: CTA b serves grid find_slot(pre, b), local index
+    b - pre[g], decoded as tile (local % tx, (local / tx) % ty, local / (tx ty)).  Grids with
+    no CTAs of a kind (e.g. no band nodes) are skipped; every tile of every grid is served once."""
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        n = int(rng.integers(1, 12))
+        tiles = [tuple(int(v) for v in rng.integers(1, 6, size=3)) for _ in range(n)]
+        counts = [tx * ty * tz if rng.random() > 0.15 else 0 for tx, ty, tz in tiles]
+        pre = np.concatenate([[0], np.cumsum(counts)]).astype(int)
+        seen = set()
+        for b in range(int(pre[-1])):
+            g = _find_slot(pre, n, b)
+            assert pre[g] <= b < pre[g + 1]
+            local = b - pre[g]
+            tx, ty, _ = tiles[g]
+            seen.add((g, local % tx, (local // tx) % ty, local // (tx * ty)))
+        want = {(g, x, y, z) for g, (tx, ty, tz) in enumerate(tiles) if counts[g]
+                for x in range(tx) for y in range(ty) for z in range(tz)}
+        assert seen == want
