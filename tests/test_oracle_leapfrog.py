@@ -255,12 +255,14 @@ def test_absorbing_reflection_small():
     assert e_out / e_in < 1e-6
 
 
-def _oblique_reflection(theta_deg, top, ppw=20, w_wl=3.0, nx=4):
-    """|reflected| / |incident| envelope of a TE plane-wave packet (E along y, k in the x-z plane
-    at theta from z) hitting the z+ face `top`.  The packet is periodic in x with the phase
-    k_x L_x (phase-shifted periodic SAT, a complex field as two real blocks) and uniform in y;
-    E^0 only, so half of it travels up.  Envelopes at a probe between the packet and the face,
-    before and after the reflection; the z- face is far enough that its echo arrives later."""
+def _oblique_reflection(theta_deg, top, ppw=20, w_wl=3.0, nx=4, comp=EY):
+    """|reflected| / |incident| envelope of a plane-wave packet (k in the x-z plane at theta from
+    z) hitting the z+ face `top`: TE with comp = E_y (E^0 only), TM with comp = H_y (H^{-1/2}
+    only); either is divergence-free and splits into an up- and a down-going half.  The packet
+    is periodic in x with the phase k_x L_x (phase-shifted periodic SAT, a complex field as two
+    real blocks) and uniform in y.  Envelopes of comp at a probe between the packet and the
+    face, before and after the reflection; the z- face is far enough that its echo arrives
+    later."""
     h = 1e-3
     lam = ppw * h
     w = w_wl * lam
@@ -275,15 +277,16 @@ def _oblique_reflection(theta_deg, top, ppw=20, w_wl=3.0, nx=4):
     kx, kz = k * math.sin(th), k * math.cos(th)
     oracle.connect_phase(re, im, 0, kx * nx * h)
     oracle.connect_phase(re, im, 1, 0.0)
-    shp = re.shape(EY)                            # E_y: x and z on the plus grid
-    z = np.arange(shp[0]) * h
-    x = np.arange(shp[2]) * h
+    shp = re.shape(comp)
+    plus = ((1, 0, 1) if comp == EY else (0, 1, 0))   # Table I: E_y (x+, y-, z+), H_y (x-, y+, z-)
+    z = _grid_nodes(n[2], h, plus[2])
+    x = _grid_nodes(n[0], h, plus[0])
     env = np.exp(-((z - kc * h) / w) ** 2) * np.cos(kz * (z - kc * h))
     f = env[:, None, None] * np.ones(shp) * np.exp(-1j * kx * x)[None, None, :]
-    re.set_field(EY, np.ascontiguousarray(f.real))
-    im.set_field(EY, np.ascontiguousarray(f.imag))
+    re.set_field(comp, np.ascontiguousarray(f.real))
+    im.set_field(comp, np.ascontiguousarray(f.imag))
     for b in (re, im):
-        b.add_probe(EY, 0, 1, kc + gap)
+        b.add_probe(comp, 0 if comp == EY else 1, 1, kc + gap)
     vz = 299792458.0 * dt * math.cos(th)         # packet (group) speed along z, per step
     steps = int(4.5 * gap * h / vz)
     for b in (re, im):
@@ -307,6 +310,20 @@ def test_absorbing_oblique_reflection_closed_form(theta):
     c = math.cos(math.radians(theta))
     expect = (1 - c) / (1 + c)
     assert abs(r_abs / r_pec - expect) < 0.1 * expect, (r_abs, r_pec, expect)
+
+
+def test_absorbing_oblique_reflection_tm():
+    """The same closed form for TM incidence (H along y): the face's other tangential pair,
+    (E_x, H_y), with the opposite curl sign, and a normal E component at the face.  The
+    magnitude is again (1 - cos theta) / (1 + cos theta).  This pair's discrete reflection
+    converges more slowly: at 45 degrees it is 0.223 at 20 points per wavelength and 0.172 at 40,
+    against 0.1716.  The pin is 40 points per wavelength, a packet of 2 wavelengths, within
+    5 % (measured 1.2 %)."""
+    r_abs = _oblique_reflection(45, ABSORBING, ppw=40, w_wl=2.0, comp=HY)
+    r_pec = _oblique_reflection(45, PEC, ppw=40, w_wl=2.0, comp=HY)
+    c = math.cos(math.radians(45))
+    expect = (1 - c) / (1 + c)
+    assert abs(r_abs / r_pec - expect) < 0.05 * expect, (r_abs, r_pec, expect)
 
 
 def _fresnel_normal(two_blocks, er2=4.0, ppw=20, w_wl=3.0):
