@@ -384,6 +384,68 @@ def test_dielectric_step_fresnel(two_blocks):
     assert abs(T - 2.0 / 3.0) < 0.06, T
 
 
+def _oblique_te_echo(theta_deg, dielectric, er2=4.0, ppw=20, w_wl=2.0, nx=4):
+    """Envelope of the echo over the incident envelope of a TE packet (E_y, k in the x-z plane at
+    theta, periodic in x with phase k_x L_x: a complex field as two real blocks) that meets, at
+    z = zi, either a second pair of blocks of eps_r = er2 joined by the interface SAT
+    (dielectric=True) or a PEC face (dielectric=False)."""
+    h = 1e-3
+    lam = ppw * math.sqrt(er2) * h                # ppw points per wavelength in the dense medium
+    w = w_wl * lam
+    th = math.radians(theta_deg)
+    k = 2 * math.pi / lam
+    kx, kz = k * math.sin(th), k * math.cos(th)
+    gap = int(round(2.5 * w / h))
+    kc, ki = 3 * gap, 5 * gap                     # packet centre, plane of the interface / wall
+    dt = oracle.dt_cfl(0.95, h, h, h)
+    # z+ face of the low pair: PEC, replaced by the interface when the pair is connected
+    low = [oracle.Block((nx, 4, ki), (h,) * 3, dt, (PEC, PEC, PEC, PEC, ABSORBING, PEC)) for _ in range(2)]
+    blocks = [low]
+    if dielectric:
+        high = [oracle.Block((nx, 4, 2 * gap), (h,) * 3, dt, (PEC, PEC, PEC, PEC, PEC, ABSORBING),
+                             eps_r=np.full((2 * gap, 4, nx), er2)) for _ in range(2)]
+        for r in range(2):
+            oracle.connect(low[r], 5, high[r], 4)
+        blocks.append(high)
+    for pair in blocks:
+        oracle.connect_phase(pair[0], pair[1], 0, kx * nx * h)
+        oracle.connect_phase(pair[0], pair[1], 1, 0.0)
+    shp = low[0].shape(EY)
+    z = np.arange(shp[0]) * h
+    x = np.arange(shp[2]) * h
+    env = np.exp(-((z - kc * h) / w) ** 2) * np.cos(kz * (z - kc * h))
+    f = env[:, None, None] * np.ones(shp) * np.exp(-1j * kx * x)[None, None, :]
+    low[0].set_field(EY, np.ascontiguousarray(f.real))
+    low[1].set_field(EY, np.ascontiguousarray(f.imag))
+    vz = 299792458.0 * dt * math.cos(th)
+    steps = int(4.5 * gap * h / vz)
+    for b in low:
+        b.add_probe(EY, 0, 1, kc + gap)
+    for pair in blocks:
+        for b in pair:
+            b.reserve_probes(steps)
+    oracle.step([b for pair in blocks for b in pair], steps)
+    sig = np.abs(low[0].probes()[0] + 1j * low[1].probes()[0])
+    mid = int(2 * gap * h / vz)
+    return sig[mid:].max() / sig[:mid].max()
+
+
+def test_interface_oblique_fresnel_te():
+    """Across two blocks joined by the interface SAT, eps_r 1 -> 4, a TE wave at 60 degrees is
+    reflected with |R| = (n1 cos ti - n2 cos tt) / (n1 cos ti + n2 cos tt) = 0.5657 (Snell:
+    sin tt = sin ti / 2).  This exercises the (E_y, H_x) pair of the interface together with the
+    phase-shifted periodic faces.  The fixed period in x gives each spectral component of the
+    packet its own angle, so the packet spreads along z.  The echo is therefore taken relative to
+    a PEC wall in the same place, as in the absorbing test.  At 20 points per wavelength this
+    gives 0.5646, within 2 % (measured 0.2 %; 0.1-0.5 % at 0, 30 and 45 degrees)."""
+    r_die = _oblique_te_echo(60, True)
+    r_pec = _oblique_te_echo(60, False)
+    ti = math.radians(60)
+    tt = math.asin(math.sin(ti) / 2.0)
+    expect = abs((math.cos(ti) - 2.0 * math.cos(tt)) / (math.cos(ti) + 2.0 * math.cos(tt)))
+    assert abs(r_die / r_pec - expect) < 0.02 * expect, (r_die, r_pec, expect)
+
+
 # SI constants, typed here rather than taken from the oracle (CODATA 2018)
 _C0 = 299792458.0
 _MU0 = 1.25663706212e-6
