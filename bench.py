@@ -321,9 +321,25 @@ def cpu_baseline(args, budget=15.0):
     t0 = time.perf_counter()
     oracle.step([blk], n)
     t1 = time.perf_counter()
-    return {"value": cells * n / (t1 - t0) / 1e9, "unit": "Gcell-updates/s", "cores": oracle.get_threads(),
+    line = {"value": cells * n / (t1 - t0) / 1e9, "unit": "Gcell-updates/s", "cores": oracle.get_threads(),
             "kind": "oracle", "sample": f"{n} leapfrog steps of the full {w.name} grid (FP64 C oracle)",
             "seconds": t1 - t0}
+    # the same oracle on one core, a shorter bounded sample (steps continue from the state above)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.step([blk], 1)
+        t1 = time.perf_counter()
+        n1 = max(1, min(args.steps, int(budget / 3 / max(t1 - t0, 1e-6))))
+        if n1 > 1:
+            t0 = time.perf_counter()
+            oracle.step([blk], n1)
+            t1 = time.perf_counter()
+        line["single_core"] = {"value": cells * n1 / (t1 - t0) / 1e9, "cores": 1,
+                               "sample": f"{n1} leapfrog steps of the same grid", "seconds": t1 - t0}
+    finally:
+        oracle.set_threads(cores)
+    return line
 
 
 def run_reference(args):
