@@ -35,6 +35,7 @@ BYTES_E = 40.0      # per cell: read H (3) + E (3) + eps_r (1), write E (3), FP3
 BYTES_FUSED = 52.0  # per cell: read E (3) + H (3) + eps_r (1), write H (3) + E (3), FP32
 # FP16 field storage: the six fields move 2 bytes per value, eps_r stays FP32
 BYTES16 = {"h_update": 18.0, "e_update": 24.0, "band_h": 18.0, "band_e": 24.0, "fused_interior": 28.0}
+HBM_NOMINAL_GBS = 7900.0   # GB300 HBM3e nominal bandwidth, context beside the measured copy peak
 
 
 def parse():
@@ -287,7 +288,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": recorded_traffic(dom, w.name, depth), "algorithmic_bytes_per_cell": bpc,
-                         "cells_per_launch": ucount,
+                         "cells_per_launch": ucount, "nominal_peak": HBM_NOMINAL_GBS,
+                         "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
                          "kernel_ms": {k: v[0] for k, v in times.items()}},
             "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
