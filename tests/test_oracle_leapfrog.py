@@ -303,10 +303,11 @@ def test_absorbing_oblique_reflection_closed_form(theta):
     is the first-order characteristic condition E_t - phi eta H_t = 0, which reflects an
     obliquely incident TE wave with R = (cos theta - 1) / (cos theta + 1).  Measured as the
     reflection ratio to a PEC face in the same geometry (which cancels the envelope loss of the
-    measurement; |R| = 1 there), at 20 points per wavelength: within 10 % of the closed form
-    (measured 2 %).  A wrong phi sign, a wrong eta, or a penalty on one field only all miss it."""
-    r_abs = _oblique_reflection(theta, ABSORBING)
-    r_pec = _oblique_reflection(theta, PEC)
+    measurement; |R| = 1 there), at 20 points per wavelength with a packet of 2 wavelengths:
+    within 10 % of the closed form (measured 3.2 % at 45 and 2.1 % at 60 degrees; 2.0 % with 3
+    wavelengths).  A wrong phi sign, a wrong eta, or a penalty on one field only all miss it."""
+    r_abs = _oblique_reflection(theta, ABSORBING, w_wl=2.0)
+    r_pec = _oblique_reflection(theta, PEC, w_wl=2.0)
     c = math.cos(math.radians(theta))
     expect = (1 - c) / (1 + c)
     assert abs(r_abs / r_pec - expect) < 0.1 * expect, (r_abs, r_pec, expect)
