@@ -305,9 +305,11 @@ def test_absorbing_oblique_reflection_closed_form(theta):
     reflection ratio to a PEC face in the same geometry (which cancels the envelope loss of the
     measurement; |R| = 1 there), at 20 points per wavelength with a packet of 2 wavelengths:
     within 10 % of the closed form (measured 3.2 % at 45 and 2.1 % at 60 degrees; 2.0 % with 3
-    wavelengths).  A wrong phi sign or a penalty on one field only fails it; so does a wrong eta,
-    at 60 degrees (a doubled eta is an impedance wall 2 eta, whose reflection happens to equal
-    the correct one at 45 degrees and vanishes at 60)."""
+    wavelengths).  A wrong phi sign fails it, and so does a wrong eta at 60 degrees: a doubled
+    eta is an impedance wall 2 eta, whose reflection happens to equal the correct one at 45
+    degrees and vanishes at 60.  A penalty on the E equation only drives the same characteristic
+    to zero and passes here; the energy pins (dissipativity, energy decay, 1D reduction) fail
+    it."""
     r_abs = _oblique_reflection(theta, ABSORBING, w_wl=2.0)
     r_pec = _oblique_reflection(theta, PEC, w_wl=2.0)
     c = math.cos(math.radians(theta))
