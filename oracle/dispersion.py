@@ -58,6 +58,55 @@ def sbp_lambda(n, h, dt, alphas):
     return lam
 
 
+def sbp_lambda_axis(n, h, dt, alpha):
+    """Amplification matrix of the SBP-SAT scheme restricted to fields that are uniform in
+    x and y, for a plane wave along z (the paper's normal-incidence case: phase alpha on the
+    z faces, zero on the x and y faces).  With zero phase across x and y the periodic SAT
+    leaves such fields uniform (the operators take constants to zero and the penalty
+    differences vanish), so this subspace is invariant and its eigenvalues are eigenvalues
+    of the full Lambda.  Columns and rows: component Ex..Hz, then the z index of the
+    component's z extent; one leapfrog step of the oracle per column."""
+    re = Block(n, h, dt, (0,) * 6)
+    im = Block(n, h, dt, (0,) * 6)
+    for a, al in enumerate((0.0, 0.0, alpha)):
+        connect_phase(re, im, a, al)
+    shapes = [re.shape(c) for c in range(6)]
+    nzs = [s[0] for s in shapes]
+    offs = np.concatenate([[0], np.cumsum(nzs)]).astype(int)
+    N = int(offs[-1])
+    lam = np.zeros((N, N), complex)
+    spread = 0.0
+    for c in range(6):
+        for q in range(nzs[c]):
+            for b in (re, im):
+                for cc in range(6):
+                    b.set_field(cc, np.zeros(shapes[cc]))
+            u = np.zeros(shapes[c])
+            u[q] = 1.0
+            re.set_field(c, u)
+            step([re, im], 1)
+            for cc in range(6):
+                F = re.field(cc) + 1j * im.field(cc)
+                col = F[:, 0, 0]
+                spread = max(spread, float(np.max(np.abs(F - col[:, None, None]))))
+                lam[offs[cc]:offs[cc + 1], offs[c] + q] = col
+    return lam, spread
+
+
+def analyse_axis(n, h, cfl, k0h):
+    """Numerical wavenumber nearest k0 and its three errors for a plane wave along z on an
+    n x n x n periodic SBP-SAT cube (uniform-in-x,y subspace, so n can be large).
+    Returns (k~, (dispersion, dissipation, global), spread), spread = the largest departure
+    from x,y-uniformity seen in any column (0 up to rounding)."""
+    hh = (h, h, h)
+    dt = cfl / (C0 * math.sqrt(3.0 / (h * h)))
+    k0 = k0h / h
+    lam, spread = sbp_lambda_axis((n, n, n), hh, dt, k0 * n * h)
+    kt, _ = wavenumbers(lam, dt)
+    i = int(np.argmin(np.abs(kt - k0)))
+    return kt[i], errors(k0, kt[i]), spread
+
+
 def _bloch_fwd(F, axis, alpha, h):
     """(F[i+1] - F[i]) / h with F[n] = e^{-j alpha} F[0]."""
     up = np.roll(F, -1, axis=axis)

@@ -138,3 +138,72 @@ def test_error_largest_at_normal_incidence():
         for th, ph in ((math.pi / 4, 0.0), (math.pi / 4, math.pi / 4), (0.9553, math.pi / 4)):
             _, (_, _, g), _ = dsp.analyse(scheme, n, h, cfl, k0h, th, ph)
             assert g < g_axis, (scheme, th, ph)
+
+
+@pytest.mark.parametrize("errors_fn", ["oracle", "product"])
+def test_error_measures_closed_forms(errors_fn):
+    """Eqs. (E_DISPER)-(E_GLOB) over one wavelength lambda = 2 pi / k0, for k~ = a + j b:
+    e^{-j k0 lambda} = 1, so the dispersion error is |1 - e^{-j a lambda}| = 2 |sin(a lambda / 2)|,
+    the dissipation error |1 - r| with r = |e^{-j k~ lambda}| = e^{b lambda}, and the global
+    error follows from the law of cosines, |1 - r e^{-j a lambda}|^2 = 1 - 2 r cos(a lambda) + r^2.
+    Checked on the oracle's measures and on the GPU tool's own copy (pure arithmetic, no GPU)."""
+    if errors_fn == "oracle":
+        fn = dsp.errors
+    else:
+        from paper_2206_00638_gb300 import dispersion as gdsp
+        fn = gdsp.errors
+    k0 = 1234.5
+    lam = 2 * math.pi / k0
+    for a, b in ((k0 * 1.013, 0.0), (k0 * 0.97, -0.8), (k0 * 1.2, 0.3), (k0 * 0.5, -5.0), (k0, 0.0)):
+        disp, diss, glob = fn(k0, complex(a, b))
+        r = math.exp(b * lam)
+        assert disp == pytest.approx(2 * abs(math.sin(a * lam / 2)), abs=1e-12)
+        assert diss == pytest.approx(abs(1 - r), abs=1e-12)
+        assert glob == pytest.approx(math.sqrt(max(1 - 2 * r * math.cos(a * lam) + r * r, 0.0)), abs=1e-12)
+
+
+def test_yee_errors_follow_closed_form_wavenumber():
+    """The whole measurement chain (amplification matrix, eigenvalues, nearest wavenumber,
+    error measures) on the Yee comparator at normal incidence gives the errors of the
+    closed-form Yee wavenumber, 2 |sin(pi k~ / k0)| for dispersion and global error, 0 for
+    dissipation."""
+    h, cfl, n = 1e-3, 0.99, (4, 4, 4)
+    dt = cfl / (dsp.C0 * math.sqrt(3.0) / h)
+    for ppw in (10, 20):
+        k0h = 2 * math.pi / ppw
+        k0 = k0h / h
+        kt = 2.0 / (dsp.C0 * dt) * math.asin(dsp.C0 * dt / h * math.sin(k0h / 2))
+        _, (disp, diss, glob), _ = dsp.analyse("yee", n, h, cfl, k0h, 0.0, 0.0)
+        want = 2 * abs(math.sin(math.pi * kt / k0))
+        assert disp == pytest.approx(want, rel=1e-8) and glob == pytest.approx(want, rel=1e-8)
+        assert diss < 1e-9
+
+
+def test_axis_subspace_gives_the_full_spectrum_wavenumber():
+    """For a wave along z the x,y-uniform fields form an invariant subspace (zero phase across
+    x and y): its amplification matrix stays uniform to rounding, and the wavenumber nearest
+    k0 is the one of the full Lambda of the 4^3 cube."""
+    h, cfl = 1e-3, 0.99
+    k0h = 2 * math.pi / 20
+    kt_full, _, _ = dsp.analyse("sbp", (4, 4, 4), h, cfl, k0h, 0.0, 0.0)
+    kt_axis, _, spread = dsp.analyse_axis(4, h, cfl, k0h)
+    assert spread < 1e-12
+    assert abs(kt_axis - kt_full) < 1e-9 * abs(kt_full)
+
+
+def test_sbp_dispersion_excess_falls_as_one_over_cube_size():
+    """The interior rows of the SBP operators are the Yee differences; the periodic seam
+    (closure rows and SAT) adds a phase error per period that does not depend on the cube
+    size n.  A wavelength then crosses ppw / n seams, so the SBP-SAT dispersion error exceeds
+    the Yee error by an amount proportional to 1/n: halving it per doubling of n (lambda/20,
+    dt = 0.99 dt_max, n = 4, 8, 16), and no dissipation."""
+    h, cfl = 1e-3, 0.99
+    k0h = 2 * math.pi / 20
+    _, (d_yee, _, _), _ = dsp.analyse("yee", (4, 4, 4), h, cfl, k0h, 0.0, 0.0)
+    excess = []
+    for n in (4, 8, 16):
+        _, (d, x, _), _ = dsp.analyse_axis(n, h, cfl, k0h)
+        assert x < 1e-10
+        excess.append(d - d_yee)
+    assert all(e > 0 for e in excess)
+    assert 1.8 < excess[0] / excess[1] < 2.2 and 1.8 < excess[1] / excess[2] < 2.2
