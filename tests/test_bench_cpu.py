@@ -71,5 +71,21 @@ def test_reference_arm_runs_on_rank_zero_only():
     assert lines[1] == []
     line = json.loads(lines[0][-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 3
+    # the default block workload, the one the GPU arm measures
+    assert line["config"]["workload"] == "mixed_faces_16^3"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_clock_summary_brackets_a_short_region():
+    """A timed region shorter than the sampling period is reported through the nearest sample
+    before and after it; samples far outside it are left out."""
+    sys.path.insert(0, ROOT)
+    import bench
+    c = bench.ClockSampler(0)
+    row = lambda mhz, cap: ["0", str(mhz), "2070", "900", "0x0", "Not Active", "Not Active", "Not Active", cap]
+    c.rows = [(0.0, row(1000, "Active")), (1.0, row(2000, "Not Active")), (1.05, row(2070, "Not Active")),
+              (2.0, row(900, "Active"))]
+    s = c.summary(1.01, 1.02)
+    assert s["samples"] == 2 and s["sm_mhz"] == 2035 and s["reasons"] == []
+    assert bench.ClockSampler(0).summary(0, 1)["reasons"] == ["unsampled"]
