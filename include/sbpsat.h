@@ -24,7 +24,11 @@
  *   - Units are SI: metres, seconds, V/m, A/m, A/m^2.
  *   - Calls are asynchronous on the simulation's stream unless stated.
  *     Host buffers passed to asynchronous calls are copied before return.
+ *   - Devices: a simulation lives on the device that was current when it was
+ *     created.  A call on it makes that device current while it runs and
+ *     makes the caller's current device current again before it returns.
  */
+
 #ifndef SBPSAT_H
 #define SBPSAT_H
 
@@ -309,22 +313,30 @@ int sbp_energy_group(sbp_sim **sims, int nsims, double *W);
  * cannot call cudaMalloc: a host function enqueued on a stream may not make
  * CUDA calls that allocate, cudaFree synchronises the whole device, and some
  * embedding frameworks fix the device budget up front.  This call computes
- * the same W^n as sbp_energy with the same kernels, but keeps its per-CTA
+ * the same W^n as sbp_energy with the same kernels in the same fixed
+ * reduction order (the two give identical bits), but keeps its per-CTA
  * partial sums in a fixed array inside the library (SBP_NOALLOC_MAX_PARTIALS
  * doubles = 512 KiB, held on every GPU that loads the library until the
  * process exits) instead of the simulation's workspace, and writes W^n to
- * the caller's device pointer W_dev (one double, 8-byte aligned) without
- * synchronising.  Nothing is allocated and no allocating library routine is
- * called.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  Every call shares the array, and the array keeps the
- * last call's partial sums: calls that overlap on the GPU (different streams
+ * the caller's device pointer W_dev (one double, 8-byte aligned, in device
+ * memory of the simulation's device) without synchronising.  Nothing is
+ * allocated and no allocating library routine is called.  The array's device
+ * address is looked up when the simulation is created (sbp_create /
+ * sbp_create_in, with its device current), so this call itself makes no
+ * set-up calls.  Every call shares the array, and the array keeps the last
+ * call's partial sums: calls that overlap on the GPU (different streams
  * without ordering) race and may return wrong values.  Each call rewrites
  * every partial it reads, so nothing needs clearing between calls.  Errors:
- * SBP_EINVAL (NULL arguments), SBP_ECAPACITY (with a message on stderr) if
- * the grid needs more than SBP_NOALLOC_MAX_PARTIALS partial sums (one per
- * CTA of the H-update grid; a cross-section of about 4000 x 4000 cells
- * reaches the limit), SBP_ECUDA if the array's address cannot be obtained. */
+ * SBP_EINVAL (NULL arguments, or W_dev not device memory of the simulation's
+ * device), SBP_ESTATE (FDTD comparator), SBP_ECAPACITY (with a message on
+ * stderr; W_dev is left untouched) if the grid needs more than
+ * SBP_NOALLOC_MAX_PARTIALS partial sums.  There is one partial sum per CTA of
+ * the H-update grid: ceil((nx+2)/32) * ceil((ny+2)/8) * gz, where gz is the
+ * number of z-chunks, ceil((nz+2)/depth).  The library picks the depth to
+ * keep gz near 2432 / (the first two factors), at least 8 planes, so a
+ * cross-section of about 4000 x 4000 cells reaches the limit; a smaller
+ * depth set through the SBP_KCHUNK environment variable raises gz and
+ * reaches it with much smaller grids. */
 #define SBP_NOALLOC_MAX_PARTIALS 65536
 int sbp_energy_noalloc(sbp_sim *s, double *W_dev);
 

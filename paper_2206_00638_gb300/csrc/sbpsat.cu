@@ -44,6 +44,25 @@ constexpr double kMu0 = 1.25663706212e-6;
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Makes `device` current for the duration of a scope (an entry point) and
+// puts the caller's current device back on exit; device < 0 only saves and
+// restores (for entry points that visit several devices).
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int device)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (device >= 0 && device != prev) cudaSetDevice(device);
+    }
+    ~DeviceGuard()
+    {
+        int now = -1;
+        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
 // NVTX range for the duration of a scope (visible in a profiler's timeline;
 // a no-op when no tool is attached).
 struct Trace {
@@ -86,6 +105,7 @@ struct sbp_sim {
     float *mu = nullptr;
     double *partials = nullptr;
     long long npartials = 0;
+    double *noalloc_partials = nullptr;   // device address of the library's fixed partial-sum array
     double *escalar = nullptr;
     sbp_sim *nbr[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     int nbr_face[6] = {-1, -1, -1, -1, -1, -1};
@@ -684,25 +704,20 @@ int finalize_energy(const sbp_sim *s, double *dst)
 
 // Partial sums of sbp_energy_noalloc: a fixed array in this library, so that
 // call allocates nothing.  In host code the name is only a stand-in for the
-// symbol; its device address comes from cudaGetSymbolAddress, looked up once
-// per device with that device current.
+// symbol; its device address comes from cudaGetSymbolAddress, looked up when a
+// simulation is created, with its device current, and kept in the simulation
+// (a device reset invalidates both together).
 static __device__ __align__(256) double g_noalloc_partials[SBP_NOALLOC_MAX_PARTIALS];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double *g_noalloc_addr[kMaxDevices] = {};
-
-int noalloc_scratch(int device, double **out)
+int noalloc_scratch(double **out)
 {
-    if (device < 0 || device >= kMaxDevices) return SBP_EINVAL;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
-        void *ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
-        if (e != cudaSuccess || !ptr) return SBP_ECUDA;
-        g_noalloc_addr[device] = static_cast<double *>(ptr);
+    void *ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+    if (e != cudaSuccess || !ptr) {
+        (void)cudaGetLastError();
+        return SBP_ECUDA;
     }
-    *out = g_noalloc_addr[device];
+    *out = static_cast<double *>(ptr);
     return SBP_OK;
 }
 
@@ -772,7 +787,8 @@ int create_common(const sbp_grid_desc *d, void *stream, void *ws, size_t bytes, 
         if (!ws || bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255)) { delete s; return ws ? SBP_ECAPACITY : SBP_EINVAL; }
     }
     s->workspace = ws;
-    int rc = setup(s, d, L, static_cast<char *>(ws));
+    int rc = noalloc_scratch(&s->noalloc_partials);
+    if (!rc) rc = setup(s, d, L, static_cast<char *>(ws));
     if (rc) { if (s->own_ws) cudaFree(ws); delete s; return rc; }
     *out = s;
     return SBP_OK;
@@ -787,7 +803,6 @@ int check_group(sbp_sim **sims, int nsims)
         for (int f = 0; f < 6; f++)
             if (sims[q]->face[f] == SBP_INTERFACE && !sims[q]->nbr[f]) return SBP_ESTATE;
     }
-    cudaSetDevice(sims[0]->device);
     return SBP_OK;
 }
 
@@ -827,6 +842,7 @@ int step_group(sbp_sim **sims, int nsims, int64_t nsteps)
     if (nsteps < 0) return SBP_EINVAL;
     int rc = check_group(sims, nsims);
     if (rc) return rc;
+    DeviceGuard dg(sims[0]->device);
     for (int q = 0; q < nsims; q++) {
         sbp_sim *s = sims[q];
         if (s->energy_every > 0) {
@@ -1220,7 +1236,7 @@ int sbp_set_field(sbp_sim *s, int comp, const void *src, int is_device)
 {
     int e[3];
     if (!s || !src || extents_of(s, comp, e)) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     if (s->prec == SBP_FP32_FP16STORE) {
         // FP32 values in; stored as value / scale in FP16
         const size_t bytes = (size_t)e[0] * e[1] * e[2] * sizeof(float);
@@ -1252,7 +1268,7 @@ int sbp_get_field(sbp_sim *s, int comp, void *dst, int to_device)
 {
     int e[3];
     if (!s || !dst || extents_of(s, comp, e)) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     if (s->prec == SBP_FP32_FP16STORE) {
         // stored FP16 values times the field's scale, out as FP32
         const size_t bytes = (size_t)e[0] * e[1] * e[2] * sizeof(float);
@@ -1317,7 +1333,7 @@ int sbp_add_probe(sbp_sim *s, int comp, int i, int j, int k, int *probe_id)
 int sbp_reserve_probes(sbp_sim *s, int64_t nsteps)
 {
     if (!s || nsteps < 0) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
     if (s->probe_buf) { cudaFree(s->probe_buf); s->probe_buf = nullptr; }
     s->probe_cap = 0;
@@ -1346,19 +1362,21 @@ int sbp_step_group(sbp_sim **sims, int nsims, int64_t nsteps)
 int sbp_half_step_h(sbp_sim **sims, int nsims)
 {
     int rc = check_group(sims, nsims);
-    if (!rc)
-        for (int q = 0; q < nsims; q++)
-            if (sims[q]->fdtd) return SBP_ESTATE;
-    return rc ? rc : half_h(sims, nsims);
+    if (rc) return rc;
+    for (int q = 0; q < nsims; q++)
+        if (sims[q]->fdtd) return SBP_ESTATE;
+    DeviceGuard dg(sims[0]->device);
+    return half_h(sims, nsims);
 }
 
 int sbp_half_step_e(sbp_sim **sims, int nsims)
 {
     int rc = check_group(sims, nsims);
-    if (!rc)
-        for (int q = 0; q < nsims; q++)
-            if (sims[q]->fdtd) return SBP_ESTATE;
-    return rc ? rc : half_e(sims, nsims);
+    if (rc) return rc;
+    for (int q = 0; q < nsims; q++)
+        if (sims[q]->fdtd) return SBP_ESTATE;
+    DeviceGuard dg(sims[0]->device);
+    return half_e(sims, nsims);
 }
 
 int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out)
@@ -1367,6 +1385,7 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
     sbp_sim *one[1] = {s};
     int rc = check_group(one, 1);
     if (rc) return rc;
+    DeviceGuard dg(s->device);
     if (s->energy_every > 0) {
         rc = ensure_series(s, (s->step + nsteps) / s->energy_every + 1);
         if (rc) return rc;
@@ -1377,14 +1396,14 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
 int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step)
 {
     if (!s || trial_steps < 1) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     return autotune(s, trial_steps, chosen_depth, ms_per_step);
 }
 
 int sbp_get_probes(sbp_sim *s, double *out, int64_t cap, int64_t *nsamples)
 {
     if (!s || cap < 0 || (!out && cap > 0)) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
     const long long rec = std::min<long long>(s->step - s->probe_base, s->probe_cap);
     if (nsamples) *nsamples = rec;
@@ -1411,7 +1430,7 @@ int sbp_energy_group(sbp_sim **sims, int nsims, double *W)
         sbp_sim *s = sims[q];
         if (!s) return SBP_EINVAL;
         if (s->fdtd) return SBP_ESTATE;   // the energy of Eq. (16) is not the Yee scheme's
-        cudaSetDevice(s->device);
+        DeviceGuard dg(s->device);
         int rc = launch_h_any(s, true, false);
         if (rc) return rc;
         rc = finalize_energy(s, s->escalar);
@@ -1433,24 +1452,31 @@ int sbp_energy(sbp_sim *s, double *W)
 
 int sbp_energy_noalloc(sbp_sim *s, double *W_dev)
 {
-    if (!s || !W_dev) return SBP_EINVAL;
+    if (!s || !W_dev || (reinterpret_cast<uintptr_t>(W_dev) & 7)) return SBP_EINVAL;
     if (s->fdtd) return SBP_ESTATE;
     if (s->npartials > SBP_NOALLOC_MAX_PARTIALS) {
         std::fprintf(stderr, "sbp_energy_noalloc: grid needs %lld partial sums, limit %d\n",
                      s->npartials, SBP_NOALLOC_MAX_PARTIALS);
         return SBP_ECAPACITY;
     }
-    cudaSetDevice(s->device);
-    double *scratch = nullptr;
-    int rc = noalloc_scratch(s->device, &scratch);
-    if (rc) return rc;
-    return energy_into(s, scratch, W_dev);
+    // W_dev must be device memory of the simulation's device: a host pointer
+    // or another GPU's memory would be written through an address the
+    // kernel cannot use.
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, W_dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return SBP_EINVAL;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != s->device)
+        return SBP_EINVAL;
+    DeviceGuard dg(s->device);
+    return energy_into(s, s->noalloc_partials, W_dev);
 }
 
 int sbp_energy_series(sbp_sim *s, double *out, int64_t cap, int64_t *count)
 {
     if (!s || cap < 0 || (!out && cap > 0)) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
     if (count) *count = s->eseries_count;
     if (s->eseries_count == 0) return SBP_OK;
@@ -1466,7 +1492,7 @@ int sbp_energy_series(sbp_sim *s, double *out, int64_t cap, int64_t *count)
 int sbp_sync(sbp_sim *s)
 {
     if (!s) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
     return check_error_flag(s);
 }
@@ -1496,7 +1522,7 @@ int sbp_save(sbp_sim *s, void *host, size_t bytes)
     Trace trace("sbp_save");
     if (!s || !host) return SBP_EINVAL;
     if (bytes < ckpt_bytes(s)) return SBP_ECAPACITY;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     SBP_CUDA(cudaStreamSynchronize(s->stream));
     int rc = check_error_flag(s);
     if (rc) return rc;
@@ -1541,7 +1567,7 @@ int sbp_load(sbp_sim *s, const void *host, size_t bytes)
     const size_t fb = s->field_elems * s->esize;
     const size_t pb = (size_t)h.nprobes * (size_t)h.probe_cap * s->psize;
     if (bytes < sizeof(h) + 6 * fb + pb + (size_t)h.eseries_count * sizeof(double)) return SBP_ECAPACITY;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     int rc;
     if (h.nprobes && (!s->probe_buf || s->probe_cap != h.probe_cap)) {
         if ((rc = sbp_reserve_probes(s, h.probe_cap))) return rc;
@@ -1564,7 +1590,7 @@ int64_t sbp_step_index(const sbp_sim *s) { return s ? s->step : -1; }
 int sbp_destroy(sbp_sim *s)
 {
     if (!s) return SBP_EINVAL;
-    cudaSetDevice(s->device);
+    DeviceGuard dg(s->device);
     cudaStreamSynchronize(s->stream);
     for (int f = 0; f < 6; f++) {
         sbp_sim *nb = s->nbr[f];
@@ -1648,7 +1674,7 @@ int sbp_batch_step(sbp_batch *b, int64_t nsteps)
 {
     Trace trace("sbp_batch_step");
     if (!b || nsteps < 0) return SBP_EINVAL;
-    cudaSetDevice(b->device);
+    DeviceGuard dg(b->device);
     if (b->m.empty() || nsteps == 0) return SBP_OK;
     int rc = SBP_OK;
     if (b->dirty && (rc = batch_rebuild(b))) return rc;
@@ -1693,7 +1719,7 @@ int sbp_batch_size(const sbp_batch *b) { return b ? (int)b->m.size() : 0; }
 int sbp_batch_destroy(sbp_batch *b)
 {
     if (!b) return SBP_EINVAL;
-    cudaSetDevice(b->device);
+    DeviceGuard dg(b->device);
     cudaStreamSynchronize(b->stream);
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);

@@ -213,6 +213,8 @@ class Sim:
         d.field_scale[0], d.field_scale[1] = float(field_scale[0]), float(field_scale[1])
         self._desc = d
         self.stream = _stream_ptr(stream)
+        import torch
+        self.device = torch.cuda.current_device()   # the library creates the simulation on this device
         h_out = C.c_void_p()
         self._ws = None
         if torch_memory:
@@ -349,8 +351,10 @@ class Sim:
     def energy_noalloc(self, out):
         """Write W^n into ``out`` (a CUDA float64 tensor with one element) on the simulation's
         stream, without allocating device memory (scratch is a fixed array in the library)."""
-        if out.dtype.itemsize != 8 or not out.is_cuda:
-            raise ValueError("out must be a CUDA float64 tensor")
+        import torch
+        if (not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or not out.is_cuda
+                or out.numel() < 1 or out.device.index != self.device):
+            raise ValueError(f"out must be a float64 tensor of at least one element on cuda:{self.device}")
         _check(lib().sbp_energy_noalloc(self._h, out.data_ptr()), "sbp_energy_noalloc")
         return out
 
@@ -511,8 +515,10 @@ class Server:
         self._h = h.value
         self.meta = {}
 
-    def submit(self, spec, nsteps, cfl=0.95):
-        """spec: workloads.BlockSpec (FP32, uniform mu, >= 8 cells per axis, no interfaces)."""
+    def submit(self, spec, nsteps, cfl=0.95, energy_every=0, flags=0):
+        """spec: workloads.BlockSpec (FP32, uniform mu, >= 8 cells per axis, no interfaces).
+        energy_every > 0 turns on the FP64 energy monitor (sampled at chunk boundaries whose
+        step is a multiple of it); flags: FLAG_* of the grid descriptor."""
         d = GridDesc()
         d.nx, d.ny, d.nz = spec.n
         d.dx, d.dy, d.dz = spec.h
@@ -525,8 +531,8 @@ class Server:
             d.face[f] = int(spec.faces[f])
         d.cfl_fraction = float(cfl)
         d.precision = FP32
-        d.energy_every = 0
-        d.flags = 0
+        d.energy_every = int(energy_every)
+        d.flags = int(flags)
         srcs = (SourceDesc * max(len(spec.sources), 1))()
         for q, s in enumerate(spec.sources):
             srcs[q] = SourceDesc(s.comp, s.i, s.j, s.k, s.kind, s.amp, s.tw, s.t0, s.f)
