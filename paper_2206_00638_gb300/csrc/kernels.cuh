@@ -206,33 +206,98 @@ __device__ __forceinline__ Tri<compute_t<S>> tri_load(const S *line, long long s
     return {ldf<CG>(q), ldf<CG>(q + s), ldf<CG>(q + 2 * s)};
 }
 
+// FMA in the arithmetic type.
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
+// A row of either operator reads at most three consecutive entries u_a, u_b,
+// u_c of its line, with coefficients k0, k1, k2 (unit spacing).  Every kernel
+// evaluates a row as the same chain, entries in increasing index order:
+//   d = k0 u_a;  d = fma(k1, u_b, d);  d = fma(k2, u_c, d).
+// A zero coefficient leaves d unchanged, and an interior row (-1, 1, 0)
+// gives u_b - u_a exactly as a subtraction does, so the interior fast paths
+// (plain differences), the one-pass kernel's x-end windows (four entries,
+// zeros outside the row) and the general path all produce the same bits.
+template <typename T>
+__device__ __forceinline__ T row_chain(const T k[3], T a, T b, T c)
+{
+    T d = k[0] * a;
+    d = fma_t(k[1], b, d);
+    return fma_t(k[2], c, d);
+}
+
 // D- : x+ (n+1 values) -> x- (n+2 rows).  First entry read by row r.
 __device__ __forceinline__ int dminus_start(int r, int n)
 {
     return (r == 0 || r == 2) ? 0 : (r == n - 1 || r == n + 1) ? n - 2 : r - 1;
 }
+// Coefficients of row r of D- on the entries at dminus_start(r, n) (Appendix).
+template <typename T>
+__device__ __forceinline__ void dminus_coefs(int r, int n, T k[3])
+{
+    if (r == 2) { k[0] = T(-0.2); k[1] = T(-0.6); k[2] = T(0.8); }              // (4u2 - 3u1 - u0) / 5
+    else if (r == n - 1) { k[0] = T(-0.8); k[1] = T(0.6); k[2] = T(0.2); }      // (u_n + 3u_{n-1} - 4u_{n-2}) / 5
+    else if (r == n + 1) { k[0] = T(0); k[1] = T(-1); k[2] = T(1); }            // u_n - u_{n-1}
+    else { k[0] = T(-1); k[1] = T(1); k[2] = T(0); }                            // rows 0 (u1 - u0), 1, 3..n-2, n
+}
 // Row r of D- from the entries gathered at dminus_start(r, n).
 template <typename T>
 __device__ __forceinline__ T dminus_eval(const Tri<T> &u, int r, int n)
 {
-    if (r == 0) return u.b - u.a;                                          // u1 - u0
-    if (r == 2) return (T(4) * u.c - T(3) * u.b - u.a) * T(0.2);           // (4u2 - 3u1 - u0) / 5
-    if (r == n - 1) return (u.c + T(3) * u.b - T(4) * u.a) * T(0.2);       // (u_n + 3u_{n-1} - 4u_{n-2}) / 5
-    if (r == n + 1) return u.c - u.b;                                      // u_n - u_{n-1}
-    return u.b - u.a;                                                      // rows 1, 3..n-2, n: u_r - u_{r-1}
+    T k[3];
+    dminus_coefs(r, n, k);
+    return row_chain(k, u.a, u.b, u.c);
 }
 
 // D+ : x- (n+2 values) -> x+ (n+1 rows).  First entry read by row r.
 __device__ __forceinline__ int dplus_start(int r, int n) { return r <= 1 ? 0 : r >= n - 1 ? n - 1 : r; }
+// Coefficients of row r of D+ on the entries at dplus_start(r, n) (Appendix).
+template <typename T>
+__device__ __forceinline__ void dplus_coefs(int r, int n, T k[3])
+{
+    if (r == 0) { k[0] = T(-1); k[1] = T(0.5); k[2] = T(0.5); }                 // (v1 + v2)/2 - v0
+    else if (r == 1) { k[0] = T(-0.5); k[1] = T(-0.25); k[2] = T(0.75); }       // 3v2/4 - v0/2 - v1/4
+    else if (r == n - 1) { k[0] = T(-0.75); k[1] = T(0.25); k[2] = T(0.5); }    // v_n/4 + v_{n+1}/2 - 3v_{n-1}/4
+    else if (r == n) { k[0] = T(-0.5); k[1] = T(-0.5); k[2] = T(1); }           // v_{n+1} - (v_{n-1} + v_n)/2
+    else { k[0] = T(-1); k[1] = T(1); k[2] = T(0); }                            // rows 2..n-2: v_{r+1} - v_r
+}
 // Row r of D+ from the entries gathered at dplus_start(r, n).
 template <typename T>
 __device__ __forceinline__ T dplus_eval(const Tri<T> &v, int r, int n)
 {
-    if (r == 0) return T(0.5) * (v.b + v.c) - v.a;                         // (v1 + v2)/2 - v0
-    if (r == 1) return T(0.75) * v.c - T(0.5) * v.a - T(0.25) * v.b;       // 3v2/4 - v0/2 - v1/4
-    if (r == n - 1) return T(0.25) * v.b + T(0.5) * v.c - T(0.75) * v.a;   // v_n/4 + v_{n+1}/2 - 3v_{n-1}/4
-    if (r == n) return v.c - T(0.5) * (v.a + v.b);                         // v_{n+1} - (v_{n-1} + v_n)/2
-    return v.b - v.a;                                                      // rows 2..n-2: v_{r+1} - v_r
+    T k[3];
+    dplus_coefs(r, n, k);
+    return row_chain(k, v.a, v.b, v.c);
+}
+
+// SAT helpers shared by every kernel that evaluates a face node, so that all
+// of them round alike.
+// Penalty value of an interface face: the partner's field at its face node,
+// or e^{-+j alpha} times the complex partner (real and imaginary simulations).
+template <bool CG, typename T, typename S>
+__device__ __forceinline__ T link_value(const Link &L, int u, long long on)
+{
+    T nv = ldf<CG>(static_cast<const S *>(L.F[u]) + on);
+    if (L.G[u]) nv = fma_t(T(L.w[1]), T(ldf<CG>(static_cast<const S *>(L.G[u]) + on)), T(L.w[0]) * nv);
+    return nv;
+}
+// Characteristic impedance eta0 sqrt(mu_r / eps_r) at the node.
+template <typename T>
+__device__ __forceinline__ T node_eta(double eta0, T mr, T er) { return T(eta0) * sqrt(mr / er); }
+// Absorbing penalty, H side: gamma = dt eta / (2 mu h) = (1/2) ba eta, ba = dt / (mu h) in stored units.
+template <typename T>
+__device__ __forceinline__ T abs_gamma_h(T ba, T eta) { return T(0.5) * ba * eta; }
+// Absorbing penalty, E side: gamma = dt / (2 eta eps h) = (a / se) / (2 eta), a = 4 dt / (eps0 h) in
+// stored units and se = 4 eps_r of the node.
+template <typename T>
+__device__ __forceinline__ T abs_gamma_e(T a, T se, T eta) { return a / se / (T(2) * eta); }
+// New value with the absorbing self term averaged over the two time levels
+// (pointwise semi-implicit): ((1 - gamma) old + inc) / (1 + gamma).
+template <typename T>
+__device__ __forceinline__ T sat_finish(T old, T inc, T gam)
+{
+    if (gam != T(0)) return fma_t(T(1) - gam, old, inc) / (T(1) + gam);
+    return old + inc;
 }
 
 // 1D norm weight (unit spacing) of node r: P+ = diag(1/2,1,...,1,1/2),
@@ -388,21 +453,16 @@ __device__ __forceinline__ T h_apply(const Params<T, S> &p, const int idx[3], lo
                     acc.add(p.B[a], pv, phi);
                     const T er = cell_sum<C, T>(p.eps, o, p.sy, p.sz) * T(0.5);
                     const T mr = MUVAR ? cell_sum<C, T>(p.mu, o, p.sy, p.sz) * T(0.5) : T(1);
-                    const T eta = T(p.eta0) * sqrt(mr / er);
-                    // gamma = dt eta / (2 mu h_a); B holds dt/(mu0 h_a) (x2 when mu varies)
+                    // B holds dt/(mu0 h_a) (x2 when mu varies)
                     const T ba = (MUVAR ? T(p.B[a].hi) * T(0.5) / mr : T(p.B[a].hi)) * p.uB;
-                    gam += T(0.5) * ba * eta;
+                    gam += abs_gamma_h(ba, node_eta(p.eta0, mr, er));
                 } else {   // interface: (phi/2)(E^A - E^B) / (mu w), w = h/2
                     const Link &L = p.link[f];
-                    const S *nf = static_cast<const S *>(L.F[u]);
                     const int nidx = L.side < 0 ? 0 : L.n_norm;      // partner E on its plus grid along a
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
                     for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
-                    T nv = ld_s(nf + on);
-                    if (L.G[u])   // e^{-+j alpha} times the complex partner, split into parts
-                        nv = T(L.w[0]) * nv + T(L.w[1]) * ld_s(static_cast<const S *>(L.G[u]) + on);
-                    acc.add(p.B[a], pv - nv, phi);
+                    acc.add(p.B[a], pv - link_value<false, T, S>(L, u, on), phi);
                 }
             }
         }
@@ -413,8 +473,7 @@ __device__ __forceinline__ T h_apply(const Params<T, S> &p, const int idx[3], lo
     } else {
         inc = plain_increment(acc);
     }
-    if (gam != T(0)) return ((T(1) - gam) * hold + inc) / (T(1) + gam);
-    return hold + inc;
+    return sat_finish(hold, inc, gam);
 }
 
 // H half-step, general path, one component at one node (Eqs. (10)-(15)).
@@ -473,20 +532,14 @@ __device__ __forceinline__ T e_apply(const Params<T, S> &p, const int idx[3], lo
                     acc.add(p.A[a], pv, phi);
                     const T er = se * T(0.25);
                     const T mr = MUVAR ? cell_sum<C, T>(p.mu, o, p.sy, p.sz) * T(0.25) : T(1);
-                    const T eta = T(p.eta0) * sqrt(mr / er);
-                    // gamma = dt / (2 eta eps h_a) = (4 dt/(eps0 h_a)) / (4 eps_r) / (2 eta)
-                    gam += T(p.A[a].hi) * p.uA / se / (T(2) * eta);
+                    gam += abs_gamma_e(T(p.A[a].hi) * p.uA, se, node_eta(p.eta0, mr, er));
                 } else {
                     const Link &L = p.link[f];
-                    const S *nf = static_cast<const S *>(L.F[u]);
                     const int nidx = L.side < 0 ? 0 : L.n_norm + 1;  // partner H on its minus grid along a
                     long long on = 0;
                     const long long ost[3] = {1, L.sy, L.sz};
                     for (int b = 0; b < 3; ++b) on += (long long)(b == a ? nidx : idx[b]) * ost[b];
-                    T nv = ldf<CG>(nf + on);
-                    if (L.G[u])
-                        nv = T(L.w[0]) * nv + T(L.w[1]) * ldf<CG>(static_cast<const S *>(L.G[u]) + on);
-                    acc.add(p.A[a], pv - nv, phi);
+                    acc.add(p.A[a], pv - link_value<CG, T, S>(L, u, on), phi);
                 }
             }
         }
@@ -503,8 +556,7 @@ __device__ __forceinline__ T e_apply(const Params<T, S> &p, const int idx[3], lo
         }
     }
     const T inc = scaled_increment(acc, se);
-    if (gam != T(0)) return ((T(1) - gam) * eold + inc) / (T(1) + gam);
-    return eold + inc;
+    return sat_finish(eold, inc, gam);
 }
 
 // E half-step, general path, one component at one node (Eqs. (7)-(9), (19)-(21)).
