@@ -135,3 +135,45 @@ def test_fp16_large_fields_with_scale():
         b.fields = [f * 1e6 for f in b.fields]
     errs, _ = _errors(w, 80, FP16, field_scale=(1e5, 1e5 / 377.0))
     assert max(errs[0]) < fp16_bound(80), errs
+
+
+@pytest.mark.parametrize("faces", [(P, P, P, P, P, P), (M, M, M, M, M, M), (A, A, A, A, A, A), (P, M, M, P, A, P),
+                                   (M, A, P, A, A, M)])
+@pytest.mark.parametrize("steps", [1, 10])
+def test_fp16_per_node_error_short_runs(faces, steps):
+    """Node by node after 1 and 10 steps: |gpu - oracle| <= 4 u (N + 1) max |F| of that field
+    (E or H).  Each update rounds once (<= u |F| / 2 per stored value) and a step mixes a node
+    with neighbours through coefficients of order the CFL number, so a handful of u per step
+    is the worst case.  A scale slip confined to boundary nodes (a wrong scale ratio in a SAT
+    coefficient, say) changes those nodes by O(1) relative and fails here, while the L2 bound
+    over the whole field would hide it."""
+    w = wl.random_box((70, 43, 37), faces=faces, seed=17, steps=steps)
+    sims = parity.gpu_run(w, steps, FP16)
+    blocks = parity.oracle_run(w, steps, sims[0].dt)
+    ref = [blocks[0].field(c) for c in range(6)]
+    got = [sims[0].field(c).astype(np.float64) for c in range(6)]
+    sims[0].close()
+    for f in (0, 1):
+        comps = range(3 * f, 3 * f + 3)
+        scale = max(np.abs(ref[c]).max() for c in comps)
+        for c in comps:
+            err = np.abs(got[c] - ref[c]).max()
+            assert err <= 4 * U16 * (steps + 1) * scale, (c, err / (U16 * scale))
+
+
+def test_fp16_per_node_error_interface():
+    """The same per-node bound across an interface SAT (two blocks joined on z)."""
+    w = wl.coupled_boxes((30, 26, 20), (30, 26, 24), axis=2, facesA=(P, A, M, P, A, P),
+                         facesB=(P, A, M, P, P, A), seed=5, steps=10)
+    sims = parity.gpu_run(w, 10, FP16)
+    blocks = parity.oracle_run(w, 10, sims[0].dt)
+    for s, b in zip(sims, blocks):
+        ref = [b.field(c) for c in range(6)]
+        got = [s.field(c).astype(np.float64) for c in range(6)]
+        for f in (0, 1):
+            comps = range(3 * f, 3 * f + 3)
+            scale = max(np.abs(ref[c]).max() for c in comps)
+            for c in comps:
+                assert np.abs(got[c] - ref[c]).max() <= 4 * U16 * 11 * scale, c
+    for s in sims:
+        s.close()
