@@ -28,7 +28,6 @@
  *     created.  A call on it makes that device current while it runs and
  *     makes the caller's current device current again before it returns.
  */
-
 #ifndef SBPSAT_H
 #define SBPSAT_H
 
@@ -232,15 +231,35 @@ int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_
  * grids fill the GPU as one large launch.  Each member keeps its own fields,
  * sources, probes and step count and gives bit-identical results to
  * stepping it alone with sbp_step.  Members must be single-block FP32
- * simulations with uniform mu, at least 8 cells per axis, no interface
- * faces and no energy monitor, created on the batch's stream.  The step
- * index lives in device memory, so with use_graphs != 0 a chunk of steps is
- * captured once as a CUDA graph and replayed while the membership and chunk
- * length stay the same. */
+ * simulations with uniform mu, at least 8 cells per axis and no interface
+ * faces, created on the batch's stream.  The step index lives in device
+ * memory, so with use_graphs != 0 a chunk of steps is captured once as a CUDA
+ * graph and replayed while the membership and chunk length stay the same.
+ * A member with an energy monitor (desc.energy_every > 0) is sampled when it
+ * joins and at the end of every sbp_batch_step call whose step is a multiple
+ * of energy_every (steps inside a chunk are not sampled; with chunks whose
+ * length divides energy_every the series equals the one taken alone, plus the
+ * sample at the final step); samples not taken read 0 in sbp_energy_series. */
 typedef struct sbp_batch sbp_batch;
-int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out);
+/* flags: SBP_BATCH_GRAPHS records each chunk (sbp_batch_step call) as a CUDA
+ * graph and replays it, updated in place when the membership changes.  By
+ * default a chunk advances the members with three launches per step (the
+ * one-pass kernel, band H and band E of every member, the band kernels on a
+ * second stream).  SBP_BATCH_PERSISTENT runs the whole chunk as one
+ * persistent launch instead: CTAs that stay resident take (step, work item)
+ * tickets in order; an item waits only for its own grid's previous step (and
+ * band E for its grid's band H), so grids at different steps overlap.  It is
+ * bit-identical to the default but slower on the serving workload (its band
+ * items run at the one-pass kernel's occupancy, 16 warps per SM, too few to
+ * hide their gather latency).  Its waits are bounded: if one gives up, the
+ * following sbp_batch_step returns SBP_ETIMEOUT. */
+#define SBP_BATCH_GRAPHS 1
+#define SBP_BATCH_PERSISTENT 2
+int sbp_batch_create(void *cuda_stream, int flags, sbp_batch **out);
 /* Add s, to stop after nsteps more steps.  The batch does not own s; remove
- * it (or destroy the batch) before destroying s. */
+ * it (or destroy the batch) before destroying s.  With an energy monitor the
+ * series is grown here to hold every sample up to the target step (an
+ * allocation and a synchronisation of the stream when it is too small). */
 int sbp_batch_add(sbp_batch *b, sbp_sim *s, int64_t nsteps);
 int sbp_batch_remove(sbp_batch *b, sbp_sim *s);
 /* Steps s still has to take in this batch. */
@@ -259,13 +278,19 @@ int sbp_batch_destroy(sbp_batch *b);
  * requests leave the batch, their probe samples are copied out and their
  * memory is returned to the stream-ordered pool.  A scheduler thread owned
  * by the server does all device work on the server's stream; results are
- * identical to running each request alone.  Times are seconds on the
- * server's monotonic clock. */
+ * identical to running each request alone.  A request with an energy monitor
+ * (grid.energy_every > 0) is sampled at chunk boundaries; when a sample is
+ * not finite or exceeds 1e6 times the largest earlier one (the signature of
+ * an unstable run: the requests start from zero fields, so sources make the
+ * energy grow legitimately, but far more slowly) the request leaves the batch
+ * with status SBP_EUNSTABLE, within two chunks of the sample, and the others
+ * run on unchanged.  Times are seconds on the server's monotonic clock. */
 typedef struct sbp_source_desc { int32_t comp, i, j, k, waveform; double amp, tw, t0, f; } sbp_source_desc;
 typedef struct sbp_probe_desc { int32_t comp, i, j, k; } sbp_probe_desc;
 typedef struct sbp_request {
     sbp_grid_desc grid;              /* FP32, eligible for batching (see sbp_batch_add); the
-                                        eps_r / mu_r arrays are copied at submit */
+                                        eps_r / mu_r arrays are copied at submit; energy_every
+                                        > 0 turns on the stability monitor */
     int64_t nsteps;
     int32_t nsources;
     const sbp_source_desc *sources;  /* copied at submit */
@@ -280,7 +305,9 @@ typedef struct sbp_result {
 } sbp_result;
 typedef struct sbp_server sbp_server;
 /* hbm_budget_bytes = 0: use 90 % of the free device memory.  chunk_steps:
- * steps per batched launch sequence (a captured graph). */
+ * steps the scheduler advances the batch by between admissions and
+ * retirements (one sbp_batch_step call, captured once as a CUDA graph and
+ * replayed until the membership changes). */
 int sbp_server_create(void *cuda_stream, size_t hbm_budget_bytes, int max_slots, int chunk_steps, sbp_server **out);
 int sbp_server_submit(sbp_server *srv, const sbp_request *req, uint64_t *ticket);
 /* SBP_OK and *res filled when the request is done, SBP_EAGAIN otherwise. */

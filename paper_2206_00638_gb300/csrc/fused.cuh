@@ -88,6 +88,10 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+__device__ __forceinline__ void mbar_inval(uint64_t *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
@@ -383,6 +387,14 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         for (int L = waited > 0 ? waited - 1 : 0; L < issued; ++L)
             (void)mbar_wait_bounded(&bar[L % kStages], (L / kStages) & 1, p.wait_limit);
     }
+    // Leave the shared memory reusable by a later tile of the same CTA (the
+    // persistent batched kernel): every thread's reads of the stages ordered
+    // before later TMA writes, and the barriers invalidated so that they can
+    // be initialised again.
+    fence_generic_to_async();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
 }
 
 template <bool SRC, typename S>
@@ -496,15 +508,15 @@ __device__ __forceinline__ void band_probes(const Params<T, S> &p, unsigned long
 // H^{n+1/2} at one band node, closure axes G: every load first (in bounds for
 // all three components: the node and its row entries lie in the padded
 // layout), then the updates.
-template <typename T, bool MUVAR, int G, typename S>
+template <typename T, bool MUVAR, int G, bool CG, typename S>
 __device__ __forceinline__ void band_h_at(const Params<T, S> &p, const int idx[3], long long o, const bool have[3],
                                           S *const outs[3], T hn[3])
 {
     Tri<T> vx[2], vy[2], vz[2];
-    h_gather<T, 3, G>(p, idx, o, vx);
-    h_gather<T, 4, G>(p, idx, o, vy);
-    h_gather<T, 5, G>(p, idx, o, vz);
-    const T hx = ld_s(p.F[3] + o), hy = ld_s(p.F[4] + o), hz = ld_s(p.F[5] + o);
+    h_gather<T, 3, G, CG>(p, idx, o, vx);
+    h_gather<T, 4, G, CG>(p, idx, o, vy);
+    h_gather<T, 5, G, CG>(p, idx, o, vz);
+    const T hx = ldf<CG>(p.F[3] + o), hy = ldf<CG>(p.F[4] + o), hz = ldf<CG>(p.F[5] + o);
     if (have[0]) st_s(outs[0] + o, hn[0] = quant<S>(h_apply<T, 3, MUVAR, G>(p, idx, o, hx, vx)));
     if (have[1]) st_s(outs[1] + o, hn[1] = quant<S>(h_apply<T, 4, MUVAR, G>(p, idx, o, hy, vy)));
     if (have[2]) st_s(outs[2] + o, hn[2] = quant<S>(h_apply<T, 5, MUVAR, G>(p, idx, o, hz, vz)));
@@ -565,7 +577,9 @@ __device__ __forceinline__ void yee_e(const Params<T, S> &p, const int idx[3], l
 }
 
 // H^{n+1/2} at the nodes of band warp w: p.F = {E^n (old), H^{n-1/2} (old)}, outs = new H.
-template <typename T, bool MUVAR, typename S>
+// CG: field reads through L2 only (the persistent batched kernel, whose other
+// CTAs wrote them earlier in the same launch).
+template <typename T, bool MUVAR, bool CG = false, typename S>
 __device__ __forceinline__ void band_h_warp(const Params<T, S> &p, const Band &b, unsigned w, int lane, long long pslot,
                                             S *const outs[3])
 {
@@ -585,11 +599,11 @@ __device__ __forceinline__ void band_h_warp(const Params<T, S> &p, const Band &b
         yee_h<T, MUVAR, 5>(p, idx, o, have[2], outs[2], hn[2]);
     } else {
         switch (G) {   // uniform per warp
-        case 4: band_h_at<T, MUVAR, 4>(p, idx, o, have, outs, hn); break;
-        case 2: band_h_at<T, MUVAR, 2>(p, idx, o, have, outs, hn); break;
-        case 6: band_h_at<T, MUVAR, 6>(p, idx, o, have, outs, hn); break;
-        case 1: band_h_at<T, MUVAR, 1>(p, idx, o, have, outs, hn); break;
-        default: band_h_at<T, MUVAR, 7>(p, idx, o, have, outs, hn); break;
+        case 4: band_h_at<T, MUVAR, 4, CG>(p, idx, o, have, outs, hn); break;
+        case 2: band_h_at<T, MUVAR, 2, CG>(p, idx, o, have, outs, hn); break;
+        case 6: band_h_at<T, MUVAR, 6, CG>(p, idx, o, have, outs, hn); break;
+        case 1: band_h_at<T, MUVAR, 1, CG>(p, idx, o, have, outs, hn); break;
+        default: band_h_at<T, MUVAR, 7, CG>(p, idx, o, have, outs, hn); break;
         }
     }
     if (pm) band_probes(p, pm, 3, i, j, pslot, hn, have);
@@ -605,15 +619,15 @@ __global__ void __launch_bounds__(256) band_h(const Params<T, S> p, const Band b
 }
 
 // E^{n+1} at one band node, closure axes G (see band_h_at).
-template <typename T, bool MUVAR, int G, typename S>
+template <typename T, bool MUVAR, int G, bool CG, typename S>
 __device__ __forceinline__ void band_e_at(const Params<T, S> &p, const int idx[3], long long o, const bool have[3],
                                           unsigned sm, double t_half, S *const outs[3], T en[3])
 {
     Tri<T> vx[2], vy[2], vz[2];
-    e_gather<T, 0, false, G>(p, idx, o, vx);
-    e_gather<T, 1, false, G>(p, idx, o, vy);
-    e_gather<T, 2, false, G>(p, idx, o, vz);
-    const T ex = ld_s(p.F[0] + o), ey = ld_s(p.F[1] + o), ez = ld_s(p.F[2] + o);
+    e_gather<T, 0, CG, G>(p, idx, o, vx);
+    e_gather<T, 1, CG, G>(p, idx, o, vy);
+    e_gather<T, 2, CG, G>(p, idx, o, vz);
+    const T ex = ldf<CG>(p.F[0] + o), ey = ldf<CG>(p.F[1] + o), ez = ldf<CG>(p.F[2] + o);
     const T sx = cell_sum<0, T>(p.eps, o, p.sy, p.sz);
     const T sy = cell_sum<1, T>(p.eps, o, p.sy, p.sz);
     const T sz = cell_sum<2, T>(p.eps, o, p.sy, p.sz);
@@ -623,7 +637,7 @@ __device__ __forceinline__ void band_e_at(const Params<T, S> &p, const int idx[3
 }
 
 // E^{n+1} at the nodes of band warp w: p.F = {E^n (old), H^{n+1/2} (new)}, outs = new E.
-template <typename T, bool MUVAR, typename S>
+template <typename T, bool MUVAR, bool CG = false, typename S>
 __device__ __forceinline__ void band_e_warp(const Params<T, S> &p, const Band &b, unsigned w, int lane, long long step,
                                             long long pslot, S *const outs[3])
 {
@@ -660,11 +674,11 @@ __device__ __forceinline__ void band_e_warp(const Params<T, S> &p, const Band &b
         yee_e<T, MUVAR, 2>(p, idx, o, have[2], sm, t_half, outs[2], en[2]);
     } else {
         switch (G) {   // uniform per warp
-        case 4: band_e_at<T, MUVAR, 4>(p, idx, o, have, sm, t_half, outs, en); break;
-        case 2: band_e_at<T, MUVAR, 2>(p, idx, o, have, sm, t_half, outs, en); break;
-        case 6: band_e_at<T, MUVAR, 6>(p, idx, o, have, sm, t_half, outs, en); break;
-        case 1: band_e_at<T, MUVAR, 1>(p, idx, o, have, sm, t_half, outs, en); break;
-        default: band_e_at<T, MUVAR, 7>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 4: band_e_at<T, MUVAR, 4, CG>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 2: band_e_at<T, MUVAR, 2, CG>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 6: band_e_at<T, MUVAR, 6, CG>(p, idx, o, have, sm, t_half, outs, en); break;
+        case 1: band_e_at<T, MUVAR, 1, CG>(p, idx, o, have, sm, t_half, outs, en); break;
+        default: band_e_at<T, MUVAR, 7, CG>(p, idx, o, have, sm, t_half, outs, en); break;
         }
     }
     if (pm) band_probes(p, pm, 0, i, j, pslot, en, have);
@@ -759,6 +773,127 @@ __global__ void __launch_bounds__(256) band_e_batched(const BatchGrid *G, const 
     const unsigned w = (unsigned)(blockIdx.x - pre[g]) * 8u + (threadIdx.x >> 5);
     if (w >= B.be.wz + B.be.wy + B.be.wx) return;
     band_e_warp<float, false>(B.pe[par], B.be, w, threadIdx.x & 31, step, step - B.probe_base, B.eout[par]);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent batched step: one launch advances every grid of a batch by K
+// steps.  CTAs take tickets from a counter in increasing order; ticket t is
+// item t mod T of step t div T.  The T items of a step go grid by grid, and
+// within a grid: its band-H items, its one-pass tiles, its band-E items (a
+// band item is kBandGroup band CTAs' worth of warps).  An item of grid g at
+// step o starts once every item of g at step o-1 has finished, a band-E item
+// also once g's band-H items of step o have (per-grid counters,
+// release/acquire).  A CTA only ever waits for items with smaller tickets,
+// which CTAs already running hold, so the launch progresses however many of
+// its CTAs are resident; with several grids a grid's next step is ready long
+// before its ticket comes up, so grids at different steps overlap.  Every
+// wait is bounded: on expiry the CTA raises the error flag, and every CTA
+// stops taking work once the flag is up.
+// ---------------------------------------------------------------------------
+constexpr int kBandGroup = 8;
+
+struct Persist {
+    unsigned *ticket;        // ticket counter (zero at launch)
+    unsigned *done;          // per grid g: [2g] items finished, [2g+1] band-H items finished (zero at launch)
+    int *error_flag;         // raised when a wait gives up
+    unsigned wait_limit;     // polls before a wait gives up
+    int K;                   // steps in this launch
+    int n;                   // grids
+    int cap;                 // prefix table stride - 1
+    int total;               // items per step, all grids
+};
+
+// Band items of a grid with `ctas` band CTAs.
+__host__ __device__ __forceinline__ int band_items(int ctas) { return (ctas + kBandGroup - 1) / kBandGroup; }
+
+// Items of grid g (band H, tiles, band E) from the three CTA prefix tables.
+__device__ __forceinline__ void grid_items(const int *pf, const int *ph, const int *pe, int g, int &nh, int &nf,
+                                           int &ne)
+{
+    nh = band_items(ph[g + 1] - ph[g]);
+    nf = pf[g + 1] - pf[g];
+    ne = band_items(pe[g + 1] - pe[g]);
+}
+
+// Wait (bounded) until *ctr >= target; false if the limit runs out or another
+// CTA has already raised the error flag (then nothing further can complete).
+__device__ __forceinline__ bool wait_count(const unsigned *ctr, unsigned target, unsigned limit, const int *error_flag)
+{
+    for (unsigned it = 0; it < limit; ++it) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) return true;
+        if ((it & 255u) == 255u && *reinterpret_cast<const volatile int *>(error_flag)) return false;
+        __nanosleep(it < 64 ? 32 : 256);
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2)
+    persistent_batched(const BatchGrid *G, const int *pre, const int *pitems, const Persist P)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ unsigned s_ticket;
+    __shared__ int s_go;
+    const int *pf = pre, *ph = pre + (P.cap + 1), *pe = pre + 2 * (P.cap + 1);
+    const unsigned end = (unsigned)P.K * (unsigned)P.total;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (;;) {
+        // no new work once a wait has given up anywhere: every later item could
+        // depend on the one that did not finish
+        if (threadIdx.x == 0)
+            s_ticket = *reinterpret_cast<const volatile int *>(P.error_flag) ? end : atomicAdd(P.ticket, 1u);
+        __syncthreads();
+        const unsigned t = s_ticket;
+        if (t >= end) return;
+        const int o = (int)(t / (unsigned)P.total);
+        int r = (int)(t - (unsigned)o * (unsigned)P.total);
+        const int g = find_slot(pitems, P.n, r);        // pitems: prefix of the grids' item counts
+        r -= pitems[g];
+        int nh, nf, ne;
+        grid_items(pf, ph, pe, g, nh, nf, ne);
+        const int kind = r < nh ? 0 : r < nh + nf ? 1 : 2;
+        r -= kind == 0 ? 0 : kind == 1 ? nh : nh + nf;
+        if (threadIdx.x == 0) {
+            const unsigned items_g = (unsigned)(nh + nf + ne);
+            bool ok = o == 0 || wait_count(&P.done[2 * g], (unsigned)o * items_g, P.wait_limit, P.error_flag);
+            if (ok && kind == 2)
+                ok = wait_count(&P.done[2 * g + 1], (unsigned)(o + 1) * (unsigned)nh, P.wait_limit, P.error_flag);
+            if (!ok) atomicExch(P.error_flag, 1);
+            // the tiles' TMA loads (async proxy) read what other CTAs stored
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            s_go = ok;
+        }
+        __syncthreads();
+        if (!s_go) return;
+        const BatchGrid &B = G[g];
+        long long step;
+        int par;
+        if (batch_state(B, o, step, par)) {
+            if (kind == 1) {
+                const int tx = B.tiles[0], ty = B.tiles[1];
+                fused_body<true, float>(B.maps[par], B.fp[par], step, step - B.probe_base, r % tx, (r / tx) % ty,
+                                        r / (tx * ty), smem_raw);
+            } else if (kind == 0) {
+                const unsigned nw = B.bh.wz + B.bh.wy + B.bh.wx;
+                for (unsigned w = (unsigned)r * (8u * kBandGroup) + (unsigned)warp;
+                     w < nw && w < (unsigned)(r + 1) * (8u * kBandGroup); w += 8u)
+                    band_h_warp<float, false, true>(B.ph[par], B.bh, w, lane, step - B.probe_base, B.hout[par]);
+            } else {
+                const unsigned nw = B.be.wz + B.be.wy + B.be.wx;
+                for (unsigned w = (unsigned)r * (8u * kBandGroup) + (unsigned)warp;
+                     w < nw && w < (unsigned)(r + 1) * (8u * kBandGroup); w += 8u)
+                    band_e_warp<float, false, true>(B.pe[par], B.be, w, lane, step, step - B.probe_base,
+                                                    B.eout[par]);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (kind == 0) atomicAdd(&P.done[2 * g + 1], 1u);
+            atomicAdd(&P.done[2 * g], 1u);
+        }
+    }
 }
 
 __global__ void batch_advance(const BatchGrid *G, int n, long long k)

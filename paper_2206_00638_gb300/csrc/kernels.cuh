@@ -410,7 +410,8 @@ __device__ __forceinline__ void block_sum_to(double v, double *dst)
 // Entries of E read by the two curl terms of H component C at node idx.
 // G: bit a set when the node may lie on a closure row or face along axis a;
 // along the other axes the node is interior and the row is u_r - u_{r-1}.
-template <typename T, int C, int G = 7, typename S = T>
+// CG: read through L2 only (fields another CTA of the same launch wrote).
+template <typename T, int C, int G = 7, bool CG = false, typename S = T>
 __device__ __forceinline__ void h_gather(const Params<T, S> &p, const int idx[3], long long o, Tri<T> v[2])
 {
 #pragma unroll
@@ -418,10 +419,10 @@ __device__ __forceinline__ void h_gather(const Params<T, S> &p, const int idx[3]
         const int u = curl_comp(C, t), a = curl_axis(C, t);
         const long long st = a == 0 ? 1 : a == 1 ? p.sy : p.sz;
         if ((G >> a) & 1) {
-            v[t] = tri_load<false>(p.F[u] + (o - idx[a] * st), st, dminus_start(idx[a], p.n[a]));
+            v[t] = tri_load<CG>(p.F[u] + (o - idx[a] * st), st, dminus_start(idx[a], p.n[a]));
         } else {
-            v[t].a = ld_s(p.F[u] + o - st);
-            v[t].b = ld_s(p.F[u] + o);
+            v[t].a = ldf<CG>(p.F[u] + o - st);
+            v[t].b = ldf<CG>(p.F[u] + o);
             v[t].c = v[t].b;
         }
     }

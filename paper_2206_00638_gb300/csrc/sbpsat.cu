@@ -599,6 +599,7 @@ int set_fused_smem_attr()
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half>, attr, sbp::kFusedSmemH));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half>, attr, sbp::kFusedSmemH));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched, attr, sbp::kFusedSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::persistent_batched, attr, sbp::kFusedSmem));
         done[dev] = true;
     }
     return SBP_OK;
@@ -752,6 +753,7 @@ int ensure_series(sbp_sim *s, long long need)
     long long cap = std::max(need, 2 * s->eseries_cap + 16);
     double *nb = nullptr;
     SBP_CUDA(cudaMalloc(&nb, cap * sizeof(double)));
+    SBP_CUDA(cudaMemsetAsync(nb, 0, cap * sizeof(double), s->stream));   // samples not taken read 0
     if (s->eseries && s->eseries_count > 0)
         SBP_CUDA(cudaMemcpyAsync(nb, s->eseries, s->eseries_count * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
     SBP_CUDA(cudaStreamSynchronize(s->stream));
@@ -1029,6 +1031,7 @@ struct sbp_batch {
     struct Member {
         sbp_sim *s;
         long long target;        // absolute step index at which the member stops
+        double *mirror;          // pinned host copy of the latest energy sample (serving), or null
     };
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on (capture runs nothing)
@@ -1037,18 +1040,25 @@ struct sbp_batch {
     int device = 0;
     std::vector<Member> m;
     sbp::BatchGrid *d_grids = nullptr;
-    int *d_pre = nullptr;               // three prefix tables of cap+1 ints: fused, band H, band E
+    int *d_pre = nullptr;               // four prefix tables of cap+1 ints: fused, band H, band E CTAs,
+                                        // persistent-kernel items
     long long *d_counters = nullptr;
     int cap = 0;
     int nf = 0, nh = 0, ne = 0;         // CTAs per launch
+    int ni = 0;                         // persistent-kernel items per step
     sbp::BatchGrid *h_grids = nullptr;  // pinned staging of the uploads
     int *h_pre = nullptr;
     long long *h_counters = nullptr;
     cudaEvent_t staged = nullptr;       // the last upload has left the staging buffers
     bool dirty = true;
     bool use_graph = true;
+    bool persistent = false;            // one persistent launch per chunk (else three launches per step)
+    unsigned *d_sched = nullptr;        // persistent kernel: ticket counter, 2 counters per member, error flag
+    int *h_err = nullptr;               // pinned copy of the persistent kernel's error flag
+    int resident = 0;                   // CTAs of the persistent kernel resident at once
     cudaGraphExec_t gexec = nullptr;
     long long gK = 0;
+    bool gstale = false;                // membership changed since gexec was recorded
 };
 
 namespace {
@@ -1067,10 +1077,14 @@ int batch_reserve(sbp_batch *b, int n)
     b->d_grids = nullptr; b->d_pre = nullptr; b->d_counters = nullptr;
     b->h_grids = nullptr; b->h_pre = nullptr; b->h_counters = nullptr;
     SBP_CUDA(cudaMalloc(&b->d_grids, sizeof(sbp::BatchGrid) * cap));
-    SBP_CUDA(cudaMalloc(&b->d_pre, sizeof(int) * 3 * (cap + 1)));
+    SBP_CUDA(cudaMalloc(&b->d_pre, sizeof(int) * 4 * (cap + 1)));
     SBP_CUDA(cudaMalloc(&b->d_counters, sizeof(long long) * cap));
+    if (b->d_sched) cudaFree(b->d_sched);
+    b->d_sched = nullptr;
+    SBP_CUDA(cudaMalloc(&b->d_sched, sizeof(unsigned) * (2 * cap + 2)));
+    SBP_CUDA(cudaMemsetAsync(b->d_sched, 0, sizeof(unsigned) * (2 * cap + 2), b->stream));
     SBP_CUDA(cudaHostAlloc((void **)&b->h_grids, sizeof(sbp::BatchGrid) * cap, cudaHostAllocDefault));
-    SBP_CUDA(cudaHostAlloc((void **)&b->h_pre, sizeof(int) * 3 * (cap + 1), cudaHostAllocDefault));
+    SBP_CUDA(cudaHostAlloc((void **)&b->h_pre, sizeof(int) * 4 * (cap + 1), cudaHostAllocDefault));
     SBP_CUDA(cudaHostAlloc((void **)&b->h_counters, sizeof(long long) * cap, cudaHostAllocDefault));
     if (!b->staged) SBP_CUDA(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
     b->cap = cap;
@@ -1091,8 +1105,8 @@ int batch_rebuild(sbp_batch *b)
     sbp::BatchGrid *hg = b->h_grids;
     int *pre = b->h_pre;
     long long *cnt = b->h_counters;
-    std::memset(pre, 0, sizeof(int) * 3 * (b->cap + 1));
-    int *pf = pre, *ph = pre + (b->cap + 1), *pe = pre + 2 * (b->cap + 1);
+    std::memset(pre, 0, sizeof(int) * 4 * (b->cap + 1));
+    int *pf = pre, *ph = pre + (b->cap + 1), *pe = pre + 2 * (b->cap + 1), *pi = pre + 3 * (b->cap + 1);
     for (int g = 0; g < n; g++) {
         sbp_sim *s = b->m[g].s;
         sbp::BatchGrid &G = hg[g];
@@ -1130,16 +1144,17 @@ int batch_rebuild(sbp_batch *b)
         pf[g + 1] = pf[g] + (int)nfg;
         ph[g + 1] = ph[g] + (int)nhg;
         pe[g + 1] = pe[g] + (int)neg;
+        pi[g + 1] = pi[g] + sbp::band_items((int)nhg) + (int)nfg + sbp::band_items((int)neg);
     }
-    b->nf = pf[n]; b->nh = ph[n]; b->ne = pe[n];
+    b->nf = pf[n]; b->nh = ph[n]; b->ne = pe[n]; b->ni = pi[n];
     if (n > 0) {
         // stream-ordered behind the chunks already queued, which read the old tables
         SBP_CUDA(cudaMemcpyAsync(b->d_grids, hg, sizeof(sbp::BatchGrid) * n, cudaMemcpyHostToDevice, b->stream));
-        SBP_CUDA(cudaMemcpyAsync(b->d_pre, pre, sizeof(int) * 3 * (b->cap + 1), cudaMemcpyHostToDevice, b->stream));
+        SBP_CUDA(cudaMemcpyAsync(b->d_pre, pre, sizeof(int) * 4 * (b->cap + 1), cudaMemcpyHostToDevice, b->stream));
         SBP_CUDA(cudaMemcpyAsync(b->d_counters, cnt, sizeof(long long) * n, cudaMemcpyHostToDevice, b->stream));
         SBP_CUDA(cudaEventRecord(b->staged, b->stream));
     }
-    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    b->gstale = true;                   // the graph is re-recorded and updated in place at the next chunk
     b->dirty = false;
     return SBP_OK;
 }
@@ -1149,21 +1164,63 @@ int batch_launch_chunk(sbp_batch *b, long long K)
 {
     const int n = (int)b->m.size();
     const int *pf = b->d_pre, *ph = b->d_pre + (b->cap + 1), *pe = b->d_pre + 2 * (b->cap + 1);
-    // per step: the one-pass interior step on the batch stream, band H then
-    // band E beside it on the side stream (band E reads only band H's output,
-    // which includes the first interior H layer), joined before the next step
-    for (long long o = 0; o < K; o++) {
-        SBP_CUDA(cudaEventRecord(b->ev_fork, b->stream));
-        if (b->nf > 0)
-            sbp::fused_batched<<<b->nf, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(b->d_grids, pf, n, (int)o);
-        SBP_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
-        if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->side>>>(b->d_grids, ph, n, (int)o);
-        if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->side>>>(b->d_grids, pe, n, (int)o);
-        SBP_CUDA(cudaEventRecord(b->ev_join, b->side));
-        SBP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
+    if (b->persistent) {
+        // one launch for the whole chunk: CTAs take (step, item) tickets in
+        // order, items wait only for their own grid's previous step (see
+        // persistent_batched); the counters start at zero
+        const long long total = b->ni;
+        if (total > 0 && K > 0) {
+            if (total * K >= (1ll << 32) - 1) return SBP_ECAPACITY;
+            SBP_CUDA(cudaMemsetAsync(b->d_sched, 0, sizeof(unsigned) * (2 * n + 1), b->stream));
+            sbp::Persist P;
+            P.ticket = b->d_sched;
+            P.done = b->d_sched + 1;
+            P.error_flag = reinterpret_cast<int *>(b->d_sched + 2 * b->cap + 1);
+            P.wait_limit = 1u << 24;
+            P.K = (int)K;
+            P.n = n;
+            P.cap = b->cap;
+            P.total = (int)total;
+            const long long grid = std::min<long long>(b->resident, total * K);
+            sbp::persistent_batched<<<(unsigned)grid, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(
+                b->d_grids, b->d_pre, b->d_pre + 3 * (b->cap + 1), P);
+            SBP_CUDA(cudaGetLastError());
+        }
+    } else {
+        // per step: the one-pass interior step on the batch stream, band H then
+        // band E beside it on the side stream (band E reads only band H's output,
+        // which includes the first interior H layer), joined before the next step
+        for (long long o = 0; o < K; o++) {
+            SBP_CUDA(cudaEventRecord(b->ev_fork, b->stream));
+            if (b->nf > 0)
+                sbp::fused_batched<<<b->nf, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(b->d_grids, pf, n, (int)o);
+            SBP_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+            if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->side>>>(b->d_grids, ph, n, (int)o);
+            if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->side>>>(b->d_grids, pe, n, (int)o);
+            SBP_CUDA(cudaEventRecord(b->ev_join, b->side));
+            SBP_CUDA(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
+        }
     }
     sbp::batch_advance<<<(n + 127) / 128, 128, 0, b->stream>>>(b->d_grids, n, K);
     SBP_CUDA(cudaGetLastError());
+    return SBP_OK;
+}
+
+// The energy monitor of a batch member: W at the member's current step into
+// its series when the step is a multiple of energy_every (the steps inside a
+// chunk are not sampled), behind the chunk on the batch's stream, and a copy
+// of the sample to the member's host mirror if it has one.
+int batch_sample_energy(sbp_batch *b, sbp_batch::Member &m)
+{
+    sbp_sim *s = m.s;
+    if (s->energy_every <= 0 || s->step % s->energy_every) return SBP_OK;
+    const long long idx = s->step / s->energy_every;
+    if (idx >= s->eseries_cap) return SBP_ECAPACITY;
+    int rc = energy_into(s, s->partials, s->eseries + idx);
+    if (rc) return rc;
+    s->eseries_count = std::max(s->eseries_count, idx + 1);
+    if (m.mirror)
+        SBP_CUDA(cudaMemcpyAsync(m.mirror, s->eseries + idx, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     return SBP_OK;
 }
 
@@ -1606,16 +1663,29 @@ int sbp_destroy(sbp_sim *s)
     return SBP_OK;
 }
 
-int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
+int sbp_batch_create(void *cuda_stream, int flags, sbp_batch **out)
 {
-    if (!out) return SBP_EINVAL;
+    if (!out || (flags & ~(SBP_BATCH_GRAPHS | SBP_BATCH_PERSISTENT))) return SBP_EINVAL;
     sbp_batch *b = new (std::nothrow) sbp_batch();
     if (!b) return SBP_ENOMEM;
     b->stream = static_cast<cudaStream_t>(cuda_stream);
-    b->use_graph = use_graphs != 0;
+    b->use_graph = (flags & SBP_BATCH_GRAPHS) != 0;
+    b->persistent = (flags & SBP_BATCH_PERSISTENT) != 0;
     cudaGetDevice(&b->device);
     int rc = set_fused_smem_attr();
     if (rc) { delete b; return rc; }
+    // CTAs of the persistent kernel that fit on the device at once
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sbp::persistent_batched, sbp::kFTY * 32,
+                                                      sbp::kFusedSmem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess ||
+        cudaHostAlloc((void **)&b->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        (void)cudaGetLastError();
+        delete b;
+        return SBP_ECUDA;
+    }
+    *b->h_err = 0;
+    b->resident = std::max(1, per_sm * sms);
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -1635,16 +1705,21 @@ int sbp_batch_create(void *cuda_stream, int use_graphs, sbp_batch **out)
 int sbp_batch_add(sbp_batch *b, sbp_sim *s, int64_t nsteps)
 {
     if (!b || !s || nsteps < 0) return SBP_EINVAL;
-    if (!s->fused_ok || s->prec != SBP_FP32 || s->fdtd || s->stream != b->stream || s->energy_every > 0 ||
-        s->device != b->device)
+    if (!s->fused_ok || s->prec != SBP_FP32 || s->fdtd || s->stream != b->stream || s->device != b->device)
         return SBP_EINVAL;
     for (int f = 0; f < 6; f++)
         if (s->face[f] == SBP_INTERFACE) return SBP_EINVAL;
     for (auto &m : b->m)
         if (m.s == s) return SBP_ESTATE;
-    b->m.push_back({s, s->step + nsteps});
+    DeviceGuard dg(b->device);
+    if (s->energy_every > 0) {
+        // room for every sample up to the target step, then the sample at the current step
+        int rc = ensure_series(s, (s->step + nsteps) / s->energy_every + 1);
+        if (rc) return rc;
+    }
+    b->m.push_back({s, s->step + nsteps, nullptr});
     b->dirty = true;
-    return SBP_OK;
+    return batch_sample_energy(b, b->m.back());
 }
 
 int sbp_batch_remove(sbp_batch *b, sbp_sim *s)
@@ -1675,12 +1750,14 @@ int sbp_batch_step(sbp_batch *b, int64_t nsteps)
     Trace trace("sbp_batch_step");
     if (!b || nsteps < 0) return SBP_EINVAL;
     DeviceGuard dg(b->device);
+    // a wait of an earlier persistent launch gave up (the flag is copied out
+    // behind every chunk)
+    if (*static_cast<volatile int *>(b->h_err)) return SBP_ETIMEOUT;
     if (b->m.empty() || nsteps == 0) return SBP_OK;
     int rc = SBP_OK;
     if (b->dirty && (rc = batch_rebuild(b))) return rc;
     if (b->use_graph) {
-        if (!b->gexec || b->gK != nsteps) {
-            if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        if (!b->gexec || b->gK != nsteps || b->gstale) {
             // record the chunk on the private stream (nothing executes during
             // capture), then launch the graph on the batch's stream, which may
             // be the legacy default stream that cannot itself be captured
@@ -1696,20 +1773,43 @@ int sbp_batch_step(sbp_batch *b, int64_t nsteps)
                 if (graph) cudaGraphDestroy(graph);
                 return rc ? rc : SBP_ECUDA;
             }
-            e = cudaGraphInstantiate(&b->gexec, graph, 0);
+            // a membership change alters only launch sizes and parameters: update
+            // the executable graph in place when the topology allows, else
+            // instantiate it anew
+            bool updated = false;
+            if (b->gexec && b->gK == nsteps) {
+                cudaGraphExecUpdateResultInfo info;
+                updated = cudaGraphExecUpdate(b->gexec, graph, &info) == cudaSuccess;
+                if (!updated) (void)cudaGetLastError();
+            }
+            if (!updated) {
+                if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+                e = cudaGraphInstantiate(&b->gexec, graph, 0);
+                if (e != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    cudaGraphDestroy(graph);
+                    b->gexec = nullptr;
+                    return SBP_ECUDA;
+                }
+            }
             cudaGraphDestroy(graph);
-            if (e != cudaSuccess) { (void)cudaGetLastError(); b->gexec = nullptr; return SBP_ECUDA; }
             b->gK = nsteps;
+            b->gstale = false;
         }
         SBP_CUDA(cudaGraphLaunch(b->gexec, b->stream));
     } else {
         if ((rc = batch_launch_chunk(b, nsteps))) return rc;
     }
-    // host bookkeeping: every member took min(nsteps, remaining) steps
+    if (b->persistent)
+        SBP_CUDA(cudaMemcpyAsync(b->h_err, b->d_sched + 2 * b->cap + 1, sizeof(int), cudaMemcpyDeviceToHost,
+                                 b->stream));
+    // host bookkeeping: every member took min(nsteps, remaining) steps; then
+    // the energy monitor of the members that reached a sampling step
     for (auto &m : b->m) {
         const long long done = std::min<long long>(nsteps, std::max<long long>(0, m.target - m.s->step));
         m.s->step += done;
         m.s->cur ^= (int)(done & 1);
+        if (done > 0 && (rc = batch_sample_energy(b, m))) return rc;
     }
     return SBP_OK;
 }
@@ -1732,6 +1832,8 @@ int sbp_batch_destroy(sbp_batch *b)
     if (b->h_grids) cudaFreeHost(b->h_grids);
     if (b->h_pre) cudaFreeHost(b->h_pre);
     if (b->h_counters) cudaFreeHost(b->h_counters);
+    if (b->d_sched) cudaFree(b->d_sched);
+    if (b->h_err) cudaFreeHost(b->h_err);
     if (b->staged) cudaEventDestroy(b->staged);
     delete b;
     return SBP_OK;

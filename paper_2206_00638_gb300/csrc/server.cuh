@@ -6,11 +6,14 @@
 // allocation nor release synchronises the device; set-up runs on a separate
 // admission stream joined to the batch stream by an event), lets admitted
 // requests join the running sbp_batch at the next chunk boundary, advances
-// the batch one chunk at a time (at most two chunks in flight; a batched
-// step covers every member in three launches, so launch overhead is already
-// amortised and no graph is re-instantiated on membership changes), and
+// the batch one chunk at a time (at most two chunks in flight; a chunk is a
+// captured graph, updated in place when the membership changes), and
 // retires finished requests: their probe samples are copied to pinned host
-// memory behind an event and their memory goes back to the pool.
+// memory behind an event and their memory goes back to the pool.  Requests
+// with an energy monitor (energy_every > 0) are sampled at chunk boundaries
+// (sbp_batch_step); the sample is mirrored to pinned host memory and checked
+// after each chunk, so a request that goes unstable leaves the batch with
+// SBP_EUNSTABLE while the others run on unchanged.
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -33,7 +36,7 @@ struct ServerRequest {
     int64_t nsteps = 0;
     std::vector<sbp_source_desc> src;
     std::vector<sbp_probe_desc> prb;
-    size_t ws_bytes = 0, probe_bytes = 0;
+    size_t ws_bytes = 0, probe_bytes = 0, energy_bytes = 0;
     double submit_s = 0, admit_s = 0, done_s = 0;
     int status = SBP_OK;
     bool done = false;
@@ -42,8 +45,29 @@ struct ServerRequest {
     void *ws = nullptr;
     void *probe_dev = nullptr;
     float *probe_host = nullptr;
+    double *energy_dev = nullptr;        // energy series (stream-ordered pool)
+    double *energy_host = nullptr;       // pinned mirror of the latest energy sample
+    double energy_max = 0.0;             // largest sample seen so far
+    int pending_status = SBP_OK;         // status to report once the retirement copy has landed
     cudaEvent_t done_ev = nullptr;
 };
+
+// Stability check of a monitored request: the latest energy sample is not
+// finite, or exceeds kEnergyGrowth times the largest earlier sample.  The
+// requests are driven by sources from zero fields, so the energy legitimately
+// grows while a source injects it; an unstable scheme grows it exponentially
+// (a mode amplified by |lambda| > 1 per step gains many orders of magnitude
+// over a chunk) and soon overflows; a source ramping up stays far below 1e6 per
+// chunk.
+constexpr double kEnergyGrowth = 1e6;
+bool energy_unstable(ServerRequest &r)
+{
+    if (!r.energy_host) return false;
+    const double v = *static_cast<volatile double *>(r.energy_host);
+    if (!std::isfinite(v) || (r.energy_max > 0.0 && v > kEnergyGrowth * r.energy_max)) return true;
+    r.energy_max = std::max(r.energy_max, v);
+    return false;
+}
 
 // Release what a simulation created without waiting for the device: its side
 // stream and events are destroyed (freed once their work completes); the
@@ -120,21 +144,46 @@ int admit(sbp_server *S, const std::shared_ptr<ServerRequest> &r)
         s->probe_cap = r->nsteps;
         s->probe_base = s->step;
     }
+    if (r->energy_bytes) {
+        // the energy series from the pool (zeroed: samples not taken read 0), so
+        // that joining the batch allocates nothing on the batch's stream
+        e = cudaMallocAsync((void **)&r->energy_dev, r->energy_bytes, S->adm);
+        if (e != cudaSuccess) { (void)cudaGetLastError(); r->energy_dev = nullptr; return cuda_fail(e); }
+        SBP_CUDA(cudaMemsetAsync(r->energy_dev, 0, r->energy_bytes, S->adm));
+        s->eseries = r->energy_dev;
+        s->eseries_cap = (long long)(r->energy_bytes / sizeof(double));
+        if (!r->energy_host) {
+            if (cudaHostAlloc((void **)&r->energy_host, sizeof(double), cudaHostAllocDefault) != cudaSuccess) {
+                (void)cudaGetLastError();
+                r->energy_host = nullptr;
+                return SBP_ENOMEM;
+            }
+        }
+        *r->energy_host = 0.0;
+    }
     cudaEvent_t ready;
     SBP_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
     SBP_CUDA(cudaEventRecord(ready, S->adm));
     SBP_CUDA(cudaStreamWaitEvent(S->stream, ready, 0));
     cudaEventDestroy(ready);
     s->stream = S->stream;
-    return sbp_batch_add(S->batch, s, r->nsteps);
+    rc = sbp_batch_add(S->batch, s, r->nsteps);
+    if (rc) return rc;
+    if (r->energy_host) S->batch->m.back().mirror = r->energy_host;
+    return SBP_OK;
 }
 
 void release_device(sbp_server *S, const std::shared_ptr<ServerRequest> &r)
 {
-    if (r->sim) { destroy_sim_async(r->sim); r->sim = nullptr; }
+    if (r->sim) {
+        r->sim->eseries = nullptr;        // the series belongs to the request (pool memory)
+        destroy_sim_async(r->sim);
+        r->sim = nullptr;
+    }
+    if (r->energy_dev) { cudaFreeAsync(r->energy_dev, S->stream); r->energy_dev = nullptr; }
     if (r->probe_dev) { cudaFreeAsync(r->probe_dev, S->stream); r->probe_dev = nullptr; }
     if (r->ws) { cudaFreeAsync(r->ws, S->stream); r->ws = nullptr; }
-    S->used -= r->ws_bytes + r->probe_bytes;
+    S->used -= r->ws_bytes + r->probe_bytes + r->energy_bytes;
 }
 
 void server_loop(sbp_server *S)
@@ -148,8 +197,11 @@ void server_loop(sbp_server *S)
             if (cudaEventQuery(r->done_ev) == cudaSuccess) {
                 cudaEventDestroy(r->done_ev);
                 r->done_ev = nullptr;
-                S->cell_updates += (double)cells_of(r->desc) * (double)r->steps;
-                finish(S, r, SBP_OK);
+                // the last energy sample has landed with the retirement copy
+                int st = r->pending_status;
+                if (!st && energy_unstable(*r)) st = SBP_EUNSTABLE;
+                if (!st) S->cell_updates += (double)cells_of(r->desc) * (double)r->steps;
+                finish(S, r, st);
                 it = S->retiring.erase(it);
             } else {
                 ++it;
@@ -159,7 +211,7 @@ void server_loop(sbp_server *S)
         // 2. admission in arrival order while a slot and the budget allow
         while (!S->pending.empty() && (int)S->active.size() < S->max_slots) {
             auto r = S->pending.front();
-            const size_t need = r->ws_bytes + r->probe_bytes;
+            const size_t need = r->ws_bytes + r->probe_bytes + r->energy_bytes;
             if (S->used + need > S->budget && !S->active.empty()) break;   // wait for memory to free up
             S->pending.pop_front();
             S->used += need;
@@ -194,11 +246,15 @@ void server_loop(sbp_server *S)
                 auto r = *it;
                 int64_t rem = 0;
                 sbp_batch_remaining(S->batch, r->sim, &rem);
-                if (rc == SBP_OK && rem > 0) { ++it; continue; }
+                // a monitored request whose energy (mirrored from a chunk that
+                // has completed) shows instability leaves the batch now
+                const bool unstable = rc == SBP_OK && energy_unstable(*r);
+                if (rc == SBP_OK && rem > 0 && !unstable) { ++it; continue; }
                 r->steps = r->nsteps - rem;
                 sbp_batch_remove(S->batch, r->sim);
                 int st = rc;
-                if (!st && r->probe_bytes) {
+                if (unstable) r->pending_status = SBP_EUNSTABLE;
+                if (!st && !unstable && r->probe_bytes) {
                     if (cudaHostAlloc((void **)&r->probe_host, r->probe_bytes, cudaHostAllocDefault) != cudaSuccess) {
                         (void)cudaGetLastError();
                         r->probe_host = nullptr;
@@ -252,7 +308,7 @@ int sbp_server_create(void *cuda_stream, size_t hbm_budget_bytes, int max_slots,
     S->budget = hbm_budget_bytes ? std::min(hbm_budget_bytes, cap) : cap;
     S->max_slots = max_slots;
     S->chunk = chunk_steps;
-    int rc = sbp_batch_create(cuda_stream, 0, &S->batch);
+    int rc = sbp_batch_create(cuda_stream, 1, &S->batch);
     if (rc) { delete S; return rc; }
     if (cudaStreamCreateWithFlags(&S->adm, cudaStreamNonBlocking) != cudaSuccess) {
         (void)cudaGetLastError();
@@ -270,7 +326,7 @@ int sbp_server_submit(sbp_server *S, const sbp_request *req, uint64_t *ticket)
     if (!S || !req || req->nsteps < 0 || req->nsources < 0 || req->nprobes < 0) return SBP_EINVAL;
     if ((req->nsources && !req->sources) || (req->nprobes && !req->probes)) return SBP_EINVAL;
     const sbp_grid_desc &d = req->grid;
-    if (d.precision != SBP_FP32 || d.mu_r || d.energy_every != 0 || d.nx < 8 || d.ny < 8 || d.nz < 8) return SBP_EINVAL;
+    if (d.precision != SBP_FP32 || d.mu_r || d.nx < 8 || d.ny < 8 || d.nz < 8) return SBP_EINVAL;
     for (int f = 0; f < 6; f++)
         if (d.face[f] == SBP_INTERFACE) return SBP_EINVAL;
     if (!desc_valid(&d)) return SBP_EINVAL;
@@ -285,7 +341,8 @@ int sbp_server_submit(sbp_server *S, const sbp_request *req, uint64_t *ticket)
     if (req->nprobes) r->prb.assign(req->probes, req->probes + req->nprobes);
     r->ws_bytes = sbp_workspace_bytes(&r->desc);
     r->probe_bytes = (size_t)req->nprobes * (size_t)req->nsteps * sizeof(float);
-    if (r->ws_bytes + r->probe_bytes > S->budget) return SBP_ENOMEM;
+    if (d.energy_every > 0) r->energy_bytes = (size_t)(req->nsteps / d.energy_every + 2) * sizeof(double);
+    if (r->ws_bytes + r->probe_bytes + r->energy_bytes > S->budget) return SBP_ENOMEM;
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) return SBP_ESTATE;
     r->ticket = S->next_ticket++;
@@ -340,6 +397,8 @@ int sbp_server_release(sbp_server *S, uint64_t ticket)
     if (it == S->all.end() || !it->second->done) return SBP_EINVAL;
     if (it->second->probe_host) cudaFreeHost(it->second->probe_host);
     it->second->probe_host = nullptr;
+    if (it->second->energy_host) cudaFreeHost(it->second->energy_host);
+    it->second->energy_host = nullptr;
     S->all.erase(it);
     return SBP_OK;
 }
@@ -376,8 +435,10 @@ int sbp_server_destroy(sbp_server *S)
     S->cv_work.notify_all();
     sbp_server_drain(S);
     if (S->worker.joinable()) S->worker.join();
-    for (auto &kv : S->all)
+    for (auto &kv : S->all) {
         if (kv.second->probe_host) cudaFreeHost(kv.second->probe_host);
+        if (kv.second->energy_host) cudaFreeHost(kv.second->energy_host);
+    }
     cudaStreamSynchronize(S->stream);
     cudaStreamSynchronize(S->adm);
     cudaStreamDestroy(S->adm);

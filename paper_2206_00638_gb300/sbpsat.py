@@ -424,10 +424,15 @@ class Batch:
     """Continuous batching of many simulations: one launch per kernel kind per step covers every
     member (wraps ``sbp_batch``).  Members must be created on the batch's stream."""
 
-    def __init__(self, stream=None, use_graphs=True):
+    GRAPHS, PERSISTENT = 1, 2
+
+    def __init__(self, stream=None, use_graphs=True, persistent=False):
+        """use_graphs: replay each chunk as a CUDA graph; persistent: one persistent launch per
+        chunk instead of three launches per step."""
         self.stream = _stream_ptr(stream)
         h = C.c_void_p()
-        _check(lib().sbp_batch_create(self.stream, 1 if use_graphs else 0, C.byref(h)), "sbp_batch_create")
+        flags = (self.GRAPHS if use_graphs else 0) | (self.PERSISTENT if persistent else 0)
+        _check(lib().sbp_batch_create(self.stream, flags, C.byref(h)), "sbp_batch_create")
         self._h = h.value
         self.members = []
 

@@ -23,8 +23,8 @@ def _workloads():
     return [wl.random_box(n, faces=f, seed=30 + q, steps=st) for q, (n, f, st) in enumerate(zip(SIZES, FACES, STEPS))]
 
 
-@pytest.mark.parametrize("use_graphs", [True, False])
-def test_batch_equals_alone_bitwise(use_graphs):
+@pytest.mark.parametrize("use_graphs, persistent", [(True, True), (False, True), (True, False), (False, False)])
+def test_batch_equals_alone_bitwise(use_graphs, persistent):
     ws = _workloads()
     alone = []
     for w in ws:
@@ -32,7 +32,7 @@ def test_batch_equals_alone_bitwise(use_graphs):
         alone.append(([s.field(c) for c in range(6)], s.probes()))
         s.close()
     stream = torch.cuda.current_stream()
-    batch = sbpsat.Batch(stream=stream, use_graphs=use_graphs)
+    batch = sbpsat.Batch(stream=stream, use_graphs=use_graphs, persistent=persistent)
     sims = []
     for w in ws:
         s = sbpsat.from_workload(w, stream=stream)[0]
@@ -74,3 +74,39 @@ def test_batch_matches_oracle():
         err = parity.compare([s], blocks)[0]
         assert max(err) < 1e-5, (w.name, err)
     batch.close()
+
+
+def test_batch_energy_monitor_matches_alone():
+    """Members with the FP64 energy monitor: sampled at the chunk boundaries whose step is a
+    multiple of energy_every (here every chunk of 16 steps), the series is the one the member
+    gives alone (every 16th step), bit for bit, and the fields stay bit-identical."""
+    ws = _workloads()[:3]
+    steps = 64
+    alone = []
+    for w in ws:
+        s = parity.gpu_run(w, steps, sbpsat.FP32, energy_every=16)[0]
+        series, rc = s.energy_series()
+        alone.append(([s.field(c) for c in range(6)], series))
+        s.close()
+    stream = torch.cuda.current_stream()
+    batch = sbpsat.Batch(stream=stream, use_graphs=True)
+    sims = []
+    for w in ws:
+        s = sbpsat.from_workload(w, stream=stream, energy_every=16)[0]
+        s.reserve_probes(steps)
+        batch.add(s, steps)
+        sims.append(s)
+    for _ in range(steps // 16):
+        batch.step(16)
+    torch.cuda.synchronize()
+    for s, (fields, series) in zip(sims, alone):
+        got, rc = s.energy_series()
+        # alone samples at the monitored steps 0, 16, 32, 48; the batch also at its last
+        # chunk boundary, step 64
+        assert len(series) == steps // 16 and len(got) == steps // 16 + 1
+        assert np.array_equal(got[:-1], series)
+        for c in range(6):
+            assert np.array_equal(s.field(c), fields[c]), c
+    batch.close()
+    for s in sims:
+        s.close()

@@ -79,3 +79,27 @@ def test_server_rejects_ineligible_requests():
     with pytest.raises(sbpsat.SbpError):
         srv.submit(small, 10)
     srv.close()
+
+
+def test_server_unstable_request_fails_alone():
+    """A request stepped beyond the stability limit (CFL 1.2, allowed by its flags) blows up:
+    its FP64 energy monitor reports SBP_EUNSTABLE and it leaves the batch early, while the
+    requests sharing the batch with it finish with probe samples bit-identical to running
+    alone."""
+    reqs = wl.serving_stream(nreq=4, seed=21, n_range=(16, 40), steps_range=(600, 600))
+    stream = torch.cuda.current_stream()
+    ref = [_alone(spec, steps, stream) for spec, steps in reqs]
+    srv = sbpsat.Server(stream=torch.cuda.Stream(), max_slots=8, chunk=16)
+    bad_spec, _ = wl.serving_stream(nreq=1, seed=5, n_range=(24, 24), steps_range=(600, 600))[0]
+    tickets = [srv.submit(spec, steps, energy_every=16) for spec, steps in reqs[:2]]
+    bad = srv.submit(bad_spec, 4000, cfl=1.2, energy_every=16, flags=sbpsat.FLAG_ALLOW_UNSTABLE)
+    tickets += [srv.submit(spec, steps, energy_every=16) for spec, steps in reqs[2:]]
+    srv.drain()
+    res_bad = srv.poll(bad)
+    assert res_bad.status == -4                     # SBP_EUNSTABLE
+    assert 0 < res_bad.steps < 4000                 # stopped early
+    for t, r, (spec, steps) in zip(tickets, ref, reqs):
+        res = srv.poll(t)
+        assert res.status == 0 and res.steps == steps
+        assert np.array_equal(srv.probes(t), r), spec.n
+    srv.close()

@@ -180,3 +180,47 @@ def test_batched_ctas_map_to_every_tile_of_every_grid_once():
         want = {(g, x, y, z) for g, (tx, ty, tz) in enumerate(tiles) if counts[g]
                 for x in range(tx) for y in range(ty) for z in range(tz)}
         assert seen == want
+
+
+def test_persistent_tickets_cover_every_item_and_wait_only_backwards():
+    """The persistent batched kernel's ticket decoding, replayed: ticket t is item t mod T of
+    step t div T; the T items go grid by grid (prefix of the grids' item counts, binary
+    search), and within a grid its band-H items, its tiles, its band-E items, a band item
+    being up to 8 band CTAs.  Every (step, kind, grid, item) is served exactly once, every
+    band CTA of every grid lies in exactly one band item, and each item's dependencies (all
+    items of its grid at the previous step; band H of its grid at its step for band E) have
+    smaller tickets, so a CTA never waits for work that no running CTA holds."""
+    group = 8
+    rng = np.random.default_rng(11)
+    for _ in range(100):
+        n = int(rng.integers(1, 7))
+        K = int(rng.integers(1, 5))
+        hct, nf, ect = (rng.integers(0, 30, size=n) for _ in range(3))
+        nh = [(c + group - 1) // group for c in hct]
+        ne = [(c + group - 1) // group for c in ect]
+        pi = np.concatenate([[0], np.cumsum([nh[g] + nf[g] + ne[g] for g in range(n)])]).astype(int)
+        T = int(pi[-1])
+        seen, ticket_of = set(), {}
+        for t in range(K * T):
+            o, r = divmod(t, T)
+            g = _find_slot(pi, n, r)
+            assert pi[g] <= r < pi[g + 1]
+            r -= pi[g]
+            kind = 0 if r < nh[g] else 1 if r < nh[g] + nf[g] else 2
+            r -= 0 if kind == 0 else nh[g] if kind == 1 else nh[g] + nf[g]
+            key = (o, kind, g, r)
+            assert key not in seen
+            seen.add(key)
+            ticket_of[key] = t
+        want = {(o, k, g, i) for o in range(K) for g in range(n)
+                for k, cnt in enumerate((nh[g], nf[g], ne[g])) for i in range(cnt)}
+        assert seen == want
+        for g in range(n):        # band CTAs (8 warps each) of an item: [item * group, (item + 1) * group)
+            for cnt, items in ((hct[g], nh[g]), (ect[g], ne[g])):
+                covered = [c for it in range(items) for c in range(it * group, min((it + 1) * group, cnt))]
+                assert covered == list(range(cnt))
+        for (o, kind, g, i), t in ticket_of.items():
+            deps = [key for key in ticket_of if key[2] == g and key[0] == o - 1]
+            if kind == 2:
+                deps += [key for key in ticket_of if key[2] == g and key[0] == o and key[1] == 0]
+            assert all(ticket_of[d] < t for d in deps)
