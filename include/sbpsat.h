@@ -212,18 +212,26 @@ int sbp_half_step_e(sbp_sim **sims, int nsims);
 int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out);
 
 /* Autotuner of the one-pass interior step (no counterpart in the paper, whose
- * own loops are CPU code): times the candidate z-block depths (planes per
- * CTA, 8..256 up to the grid's interior depth) with trial_steps (>= 1) device
- * steps each, on the simulation's stream, and keeps the fastest.  The trial
- * steps are not committed: they write the spare field set and the current
- * probe slot, which the next step overwrites, so the simulation's state and
- * step index are unchanged.  The choice is remembered for this grid shape and
- * precision and applied to simulations created later in the process.
- * *chosen_depth and *ms_per_step (optional) receive the depth and its time.
- * Synchronises the stream.  Errors: SBP_EINVAL, SBP_ESTATE (the grid does
- * not run the one-pass step, or has an interface to another block),
- * SBP_ECUDA, SBP_ETIMEOUT. */
+ * own loops are CPU code): times every candidate tile -- 8 or 16 H rows per
+ * CTA (16 when the grid has at least 15 interior rows) times z-block depths of
+ * 8..256 planes up to the grid's interior depth -- with trial_steps (>= 1)
+ * device steps each, on the simulation's stream, and keeps the fastest.  The
+ * trial steps are not committed: they write the spare field set and the
+ * current probe slot, which the next step overwrites, so the simulation's
+ * state and step index are unchanged, and the tile changes only which CTA
+ * computes a node, not its arithmetic (results are bit-identical).  The
+ * choice is remembered for this grid shape and precision and applied to
+ * simulations created later in the process (and written to the file named by
+ * SBP_TUNE_CACHE, if set).  *chosen_depth and *ms_per_step (optional) receive
+ * the depth and its time; sbp_tile reports the rows.  Synchronises the
+ * stream.  Errors: SBP_EINVAL, SBP_ESTATE (the grid does not run the
+ * one-pass step, or has an interface to another block), SBP_ECUDA,
+ * SBP_ETIMEOUT.  Batch members run 8-row tiles (a member tuned to 16 rows
+ * returns to 8 when it joins a batch). */
 int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step);
+/* Tile of the one-pass step: H rows per CTA (8 or 16) and z-block depth.
+ * SBP_ESTATE if the simulation does not run the one-pass step. */
+int sbp_tile(const sbp_sim *s, int *rows, int *depth);
 
 /* Batches: continuous batching of many simulations.  A batch advances all
  * its member simulations together, one kernel launch per kernel kind per

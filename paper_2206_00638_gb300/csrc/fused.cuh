@@ -28,24 +28,26 @@
 namespace sbp {
 
 constexpr int kFTX = 64;                 // H footprint width
-constexpr int kFTY = 8;                  // H footprint rows (= warps)
+constexpr int kFTY = 8;                  // H footprint rows (= warps) of the default tile and of batches
 #ifndef SBP_FUSED_STAGES
 #define SBP_FUSED_STAGES 4
 #endif
 constexpr int kStages = SBP_FUSED_STAGES;     // TMA pipeline depth (planes in shared memory)
-constexpr int kERows = kFTY + 1;         // E rows y0-1 .. y0+7
-constexpr int kHRows = kFTY;             // H / eps rows y0 .. y0+7
-constexpr int kHbufFloats = 2 * 3 * kFTY * kFTX;
 constexpr unsigned kWaitLimit = 1u << 22;
 
 constexpr int round128(int bytes) { return (bytes + 127) / 128 * 128; }
 
-// Shared-memory geometry of one pipeline stage for field storage type S.  A
-// TMA box starts at an x that is a multiple of 16 bytes (4 FP32 or 8 FP16
+// Shared-memory geometry of one pipeline stage for field storage type S and
+// a tile of R H rows (R warps; E is produced on the inner R-1 rows).  A TMA
+// box starts at an x that is a multiple of 16 bytes (4 FP32 or 8 FP16
 // elements) at or below x0-1 and spans the 64 columns after it: kBX columns.
+// The E box holds rows y0-1 .. y0+R-1, the H and eps boxes rows y0 .. y0+R-1.
 // The eps box (always FP32) uses the same start and width.
-template <typename S>
+template <typename S, int R = kFTY>
 struct FusedGeom {
+    static constexpr int kERows = R + 1;
+    static constexpr int kHRows = R;
+    static constexpr int kHbufFloats = 2 * 3 * R * kFTX;   // H^{n+1/2} of two planes
     static constexpr int kAlign = 16 / (int)sizeof(S);
     static constexpr int kBX = kFTX + kAlign;
     static constexpr int kEBytes = round128(kERows * kBX * (int)sizeof(S));   // one E box slot
@@ -55,9 +57,7 @@ struct FusedGeom {
     static constexpr int kTxBytes = (3 * kERows + 3 * kHRows) * kBX * (int)sizeof(S) + kHRows * kBX * 4;
     static constexpr int kSmem = kStages * kStageBytes + kHbufFloats * 4 + kStages * 8;
 };
-constexpr int kFBX = FusedGeom<float>::kBX;
 constexpr int kFusedSmem = FusedGeom<float>::kSmem;
-constexpr int kFusedSmemH = FusedGeom<__half>::kSmem;
 
 template <typename S>
 struct FusedParamsT {
@@ -139,11 +139,11 @@ struct FusedMaps {
     CUtensorMap e[3], h[3], eps;
 };
 
-template <typename S>
+template <typename S, int R>
 __device__ __forceinline__ void issue_plane(const FusedMaps &m, unsigned char *stage, uint64_t *bar, int xb, int y0,
                                             int plane)
 {
-    using Gm = FusedGeom<S>;
+    using Gm = FusedGeom<S, R>;
     mbar_expect_tx(bar, Gm::kTxBytes);
 #pragma unroll
     for (int f = 0; f < 3; ++f) tma_load_3d(stage + f * Gm::kEBytes, &m.e[f], xb, y0 - 1, plane, bar);
@@ -154,14 +154,15 @@ __device__ __forceinline__ void issue_plane(const FusedMaps &m, unsigned char *s
 
 // One CTA of the one-pass interior step: tile (bx, by) in x/y, z-chunk bz,
 // time step `step` (J is evaluated at t^{step+1/2}), probe sample `pslot`.
-template <bool SRC, typename S>
+template <bool SRC, typename S, int R = kFTY>
 __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedParamsT<S> &p, long long step,
                                            long long pslot, int bx, int by, int bz, unsigned char *smem)
 {
-    using Gm = FusedGeom<S>;
+    using Gm = FusedGeom<S, R>;
+    constexpr int kFTY = R;                        // tile rows (= warps) of this instantiation
     constexpr int kBX = Gm::kBX;
     float *hbuf = reinterpret_cast<float *>(smem + kStages * Gm::kStageBytes);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(hbuf + kHbufFloats);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(hbuf + Gm::kHbufFloats);
     // slots of a stage: E fields, H fields (storage type), eps (FP32)
     auto slotE = [&](int st, int f) { return reinterpret_cast<const S *>(smem + st * Gm::kStageBytes + f * Gm::kEBytes); };
     auto slotH = [&](int st, int f) {
@@ -190,7 +191,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     int issued = 0;                                   // planes issued (thread 0's count)
     if (threadIdx.x == 0 && !p.test_stall)
         for (; issued < kStages && issued < nplanes; ++issued)
-            issue_plane<S>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
+            issue_plane<S, R>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
     // J(t^{n+1/2}) of every source is the same at each node it reaches, so
     // warp 1 evaluates it once per CTA (FP64 waveform, rounded to FP32 once)
     // while the first planes load; it is first read after the barrier below.
@@ -248,7 +249,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     fence_generic_to_async();                         // the E carries of plane k0-1
     if (__syncthreads_or(!ok)) aborted = true;
     if (!aborted && threadIdx.x == 0 && kStages < nplanes) {   // plane k0-1 is in registers now
-        issue_plane<S>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
+        issue_plane<S, R>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
         ++issued;
     }
 #pragma unroll(sizeof(S) == 4 ? 2 : 1)   // two planes per iteration with FP32 storage (faster there, slower with FP16)
@@ -375,7 +376,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         if (threadIdx.x == 0) {
             const int nxt = q + kStages;
             if (nxt <= k1) {
-                issue_plane<S>(maps, smem + sq * Gm::kStageBytes, &bar[sq], xb, y0, nxt);
+                issue_plane<S, R>(maps, smem + sq * Gm::kStageBytes, &bar[sq], xb, y0, nxt);
                 ++issued;
             }
         }
@@ -397,12 +398,12 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
 }
 
-template <bool SRC, typename S>
-__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2)
+template <bool SRC, typename S, int R>
+__global__ void __launch_bounds__(R * 32, R >= 16 ? 1 : (kStages <= 3 ? 3 : 2))
     fused_interior(const __grid_constant__ FusedMaps maps, const FusedParamsT<S> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    fused_body<SRC, S>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+    fused_body<SRC, S, R>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

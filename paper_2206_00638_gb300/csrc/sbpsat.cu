@@ -96,6 +96,7 @@ struct sbp_sim {
     int *error_flag = nullptr;            // device flag raised by a pipeline wait that gave up
     sbp::FusedMaps maps[2];               // TMA tensor maps reading set 0 / set 1
     int fused_kchunk = 32;
+    int fused_rows = sbp::kFTY;           // tile rows of the one-pass step (8 or 16)
     dim3 fused_grid;
     bool async_setup = false;             // caller keeps host inputs alive: no stream syncs in setup
     cudaStream_t side = nullptr;          // band_h runs here, concurrently with fused_interior
@@ -136,9 +137,18 @@ struct Layout {
     dim3 grid;
     bool fused;
     int fused_kchunk;
+    int fused_rows;
     dim3 fused_grid;
     size_t total;
 };
+
+// Grid of the one-pass step for tiles of `rows` H rows and z-blocks of `depth` planes.
+dim3 fused_dims(const int n[3], int rows, int depth)
+{
+    const int tx = (n[0] - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
+    const int ty = (n[1] - 5 + rows - 2) / (rows - 1);
+    return dim3(tx, ty, (n[2] - 5 + depth - 1) / depth);
+}
 
 bool desc_valid(const sbp_grid_desc *d)
 {
@@ -170,14 +180,15 @@ bool desc_valid(const sbp_grid_desc *d)
     return true;
 }
 
-// z-block depths chosen by sbp_autotune, per grid shape and precision
+// tiles (z-block depth, rows) chosen by sbp_autotune, per grid shape and precision
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, int> g_tuned_depth;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;   // (depth, rows)
 bool g_tune_file_read = false;
 
 // Optional persistence: SBP_TUNE_CACHE names a file of JSON lines
-// {"nx": .., "ny": .., "nz": .., "precision": .., "depth": ..}, read once and
-// appended to by every tuning.  Caller holds g_tune_mu.
+// {"nx": .., "ny": .., "nz": .., "precision": .., "depth": .., "rows": ..}
+// (a line without "rows" means 8), read once and appended to by every
+// tuning.  Caller holds g_tune_mu.
 void read_tune_file()
 {
     if (g_tune_file_read) return;
@@ -188,32 +199,33 @@ void read_tune_file()
     if (!f) return;
     char line[256];
     while (std::fgets(line, sizeof(line), f)) {
-        int nx, ny, nz, prec, depth;
-        if (std::sscanf(line, " {\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d}", &nx, &ny,
-                        &nz, &prec, &depth) == 5 &&
-            depth > 0)
-            g_tuned_depth[std::make_tuple(nx, ny, nz, prec)] = depth;
+        int nx, ny, nz, prec, depth, rows = sbp::kFTY;
+        const int got = std::sscanf(line, " {\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d, \"rows\": %d}",
+                                    &nx, &ny, &nz, &prec, &depth, &rows);
+        if (got >= 5 && depth > 0 && (rows == 8 || rows == 16))
+            g_tuned[std::make_tuple(nx, ny, nz, prec)] = std::make_pair(depth, rows);
     }
     std::fclose(f);
 }
 
-void append_tune_file(int nx, int ny, int nz, int prec, int depth)
+void append_tune_file(int nx, int ny, int nz, int prec, int depth, int rows)
 {
     const char *path = std::getenv("SBP_TUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d}\n", nx, ny, nz, prec,
-                 depth);
+    std::fprintf(f, "{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d, \"rows\": %d}\n", nx, ny,
+                 nz, prec, depth, rows);
     std::fclose(f);
 }
 
-int tuned_depth(const sbp_grid_desc *d)
+// (depth, rows) chosen by sbp_autotune for this shape and precision, or (0, 0).
+std::pair<int, int> tuned_tile(const sbp_grid_desc *d)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     read_tune_file();
-    auto it = g_tuned_depth.find(std::make_tuple(d->nx, d->ny, d->nz, d->precision));
-    return it == g_tuned_depth.end() ? 0 : it->second;
+    auto it = g_tuned.find(std::make_tuple(d->nx, d->ny, d->nz, d->precision));
+    return it == g_tuned.end() ? std::make_pair(0, 0) : it->second;
 }
 
 Layout make_layout(const sbp_grid_desc *d)
@@ -248,13 +260,23 @@ Layout make_layout(const sbp_grid_desc *d)
         const long long target = 4ll * 2 * 152;        // about four waves of two CTAs per SM
         const long long chunks = std::max(1ll, (target + (long long)tx * ty - 1) / ((long long)tx * ty));
         int kcf = (int)std::max(8ll, ((long long)(d->nz - 5) + chunks - 1) / chunks);
-        if (const int t = tuned_depth(d)) kcf = t;
+        const std::pair<int, int> tt = tuned_tile(d);
+        int rows = sbp::kFTY;
+        if (tt.first) { kcf = tt.first; rows = tt.second; }
         if (const char *env = std::getenv("SBP_FUSED_KCHUNK")) {
             const int v = std::atoi(env);
             if (v > 0) kcf = v;
         }
+        if (const char *env = std::getenv("SBP_FUSED_ROWS")) {
+            const int v = std::atoi(env);
+            if (v == 8 || v == 16) rows = v;
+        }
         L.fused_kchunk = kcf;
-        L.fused_grid = dim3(tx, ty, (d->nz - 5 + kcf - 1) / kcf);
+        L.fused_rows = rows;
+        const int nn[3] = {d->nx, d->ny, d->nz};
+        L.fused_grid = fused_dims(nn, rows, kcf);
+        (void)tx;
+        (void)ty;
     }
     L.total = (L.fused ? 12 : 6) * L.field_bytes + L.cell_bytes * (d->mu_r ? 2 : 1) + L.partial_bytes + 256 + 256;
     return L;
@@ -314,18 +336,21 @@ int encode_one(CUtensorMap *m, void *base, const sbp_sim *s, int rows, int esize
     return r == CUDA_SUCCESS ? SBP_OK : SBP_ECUDA;
 }
 
+// TMA maps of both field sets for the current tile rows: E boxes of rows+1
+// rows (y0-1 .. y0+rows-1), H and eps boxes of rows rows.
 int encode_maps(sbp_sim *s)
 {
     const int es = (int)s->esize;
     const int bx = es == 2 ? sbp::FusedGeom<__half>::kBX : sbp::FusedGeom<float>::kBX;
+    const int rows = s->fused_rows;
     for (int set = 0; set < 2; set++) {
         for (int f = 0; f < 3; f++) {
-            int rc = encode_one(&s->maps[set].e[f], s->set[set][f], s, sbp::kERows, es, bx);
+            int rc = encode_one(&s->maps[set].e[f], s->set[set][f], s, rows + 1, es, bx);
             if (rc) return rc;
-            rc = encode_one(&s->maps[set].h[f], s->set[set][3 + f], s, sbp::kHRows, es, bx);
+            rc = encode_one(&s->maps[set].h[f], s->set[set][3 + f], s, rows, es, bx);
             if (rc) return rc;
         }
-        int rc = encode_one(&s->maps[set].eps, s->eps, s, sbp::kHRows, 4, bx);
+        int rc = encode_one(&s->maps[set].eps, s->eps, s, rows, 4, bx);
         if (rc) return rc;
     }
     return SBP_OK;
@@ -357,6 +382,7 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     s->npartials = L.npartials;
     s->fused_ok = L.fused;
     s->fused_kchunk = L.fused_kchunk;
+    s->fused_rows = L.fused_rows;
     s->fused_grid = L.fused_grid;
     char *p = ws;
     for (int set = 0; set < (L.fused ? 2 : 1); set++)
@@ -594,10 +620,14 @@ int set_fused_smem_attr()
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !done[dev]) {
         const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, float>, attr, sbp::kFusedSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float>, attr, sbp::kFusedSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half>, attr, sbp::kFusedSmemH));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half>, attr, sbp::kFusedSmemH));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, float, 8>, attr, sbp::FusedGeom<float, 8>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float, 8>, attr, sbp::FusedGeom<float, 8>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half, 8>, attr, sbp::FusedGeom<__half, 8>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half, 8>, attr, sbp::FusedGeom<__half, 8>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, float, 16>, attr, sbp::FusedGeom<float, 16>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float, 16>, attr, sbp::FusedGeom<float, 16>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half, 16>, attr, sbp::FusedGeom<__half, 16>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half, 16>, attr, sbp::FusedGeom<__half, 16>::kSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched, attr, sbp::kFusedSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::persistent_batched, attr, sbp::kFusedSmem));
         done[dev] = true;
@@ -615,11 +645,19 @@ int launch_fused_interior_t(sbp_sim *s)
     if (rc) return rc;
     rc = set_fused_smem_attr();
     if (rc) return rc;
-    constexpr int smem = sbp::FusedGeom<S>::kSmem;
-    if (fp.nsrc > 0)
-        sbp::fused_interior<true, S><<<s->fused_grid, sbp::kFTY * 32, smem, s->stream>>>(s->maps[old], fp);
-    else
-        sbp::fused_interior<false, S><<<s->fused_grid, sbp::kFTY * 32, smem, s->stream>>>(s->maps[old], fp);
+    if (s->fused_rows == 16) {
+        constexpr int smem = sbp::FusedGeom<S, 16>::kSmem;
+        if (fp.nsrc > 0)
+            sbp::fused_interior<true, S, 16><<<s->fused_grid, 16 * 32, smem, s->stream>>>(s->maps[old], fp);
+        else
+            sbp::fused_interior<false, S, 16><<<s->fused_grid, 16 * 32, smem, s->stream>>>(s->maps[old], fp);
+    } else {
+        constexpr int smem = sbp::FusedGeom<S, 8>::kSmem;
+        if (fp.nsrc > 0)
+            sbp::fused_interior<true, S, 8><<<s->fused_grid, 8 * 32, smem, s->stream>>>(s->maps[old], fp);
+        else
+            sbp::fused_interior<false, S, 8><<<s->fused_grid, 8 * 32, smem, s->stream>>>(s->maps[old], fp);
+    }
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
 }
@@ -955,10 +993,18 @@ int check_error_flag(sbp_sim *s)
     return v ? SBP_ETIMEOUT : SBP_OK;
 }
 
-void set_depth(sbp_sim *s, int depth)
+// Tile of the one-pass step: rows (8 or 16) and z-block depth; new rows
+// re-encode the TMA maps (their boxes are rows high).
+int set_tile(sbp_sim *s, int rows, int depth)
 {
     s->fused_kchunk = depth;
-    s->fused_grid.z = (unsigned)((s->n[2] - 5 + depth - 1) / depth);
+    if (rows != s->fused_rows) {
+        s->fused_rows = rows;
+        int rc = encode_maps(s);
+        if (rc) return rc;
+    }
+    s->fused_grid = fused_dims(s->n, rows, depth);
+    return SBP_OK;
 }
 
 // Average device time of `trials` fused steps that are not committed: each
@@ -987,10 +1033,14 @@ int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
     Trace trace("sbp_autotune");
     if (!s->fused_ok || linked_to_other(s)) return SBP_ESTATE;
     const int span = s->n[2] - 5;                      // interior E planes of the one-pass step
-    std::vector<int> cand;
-    for (int c : {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
-        if (c <= span || cand.empty()) cand.push_back(c);
-    if (std::find(cand.begin(), cand.end(), s->fused_kchunk) == cand.end()) cand.push_back(s->fused_kchunk);
+    std::vector<std::pair<int, int>> cand;             // (rows, depth)
+    for (int rows : {8, 16}) {
+        if (rows == 16 && s->n[1] - 5 < 15) continue;  // no full 16-row tile
+        for (int c : {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
+            if (c <= span || c == 8) cand.push_back(std::make_pair(rows, c));
+    }
+    const std::pair<int, int> keep = std::make_pair(s->fused_rows, s->fused_kchunk);
+    if (std::find(cand.begin(), cand.end(), keep) == cand.end()) cand.push_back(keep);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SBP_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -998,27 +1048,29 @@ int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
         cudaEventDestroy(e0);
         return SBP_ECUDA;
     }
-    const int keep = s->fused_kchunk;
-    int best = keep, rc = SBP_OK;
+    std::pair<int, int> best = keep;
+    int rc = SBP_OK;
     float best_t = 0.f;
-    for (int c : cand) {
-        set_depth(s, c);
+    for (const auto &c : cand) {
+        if ((rc = set_tile(s, c.first, c.second))) break;
         float t = 0.f;
         if ((rc = time_trials(s, trials, e0, e1, &t))) break;
         if (best_t == 0.f || t < best_t) { best_t = t; best = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    set_depth(s, rc ? keep : best);
+    const std::pair<int, int> fin = rc ? keep : best;
+    const int rc2 = set_tile(s, fin.first, fin.second);
     if (rc) return rc;
+    if (rc2) return rc2;
     if ((rc = check_error_flag(s))) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         read_tune_file();
-        g_tuned_depth[std::make_tuple(s->n[0], s->n[1], s->n[2], s->prec)] = best;
-        append_tune_file(s->n[0], s->n[1], s->n[2], s->prec, best);
+        g_tuned[std::make_tuple(s->n[0], s->n[1], s->n[2], s->prec)] = std::make_pair(best.second, best.first);
+        append_tune_file(s->n[0], s->n[1], s->n[2], s->prec, best.second, best.first);
     }
-    if (chosen) *chosen = best;
+    if (chosen) *chosen = best.second;
     if (best_ms) *best_ms = best_t;
     return SBP_OK;
 }
@@ -1111,6 +1163,9 @@ int batch_rebuild(sbp_batch *b)
         sbp_sim *s = b->m[g].s;
         sbp::BatchGrid &G = hg[g];
         std::memset(static_cast<void *>(&G), 0, sizeof(G));
+        // the batched kernels run 8-row tiles: a member tuned to another tile
+        // height returns to 8 rows (its TMA boxes are re-encoded)
+        if (s->fused_rows != sbp::kFTY && (rc = set_tile(s, sbp::kFTY, s->fused_kchunk))) return rc;
         for (int c = 0; c < 2; c++) {
             G.maps[c] = s->maps[c];
             if ((rc = make_fused_params(s, c, G.fp[c]))) return rc;
@@ -1448,6 +1503,15 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
         if (rc) return rc;
     }
     return step_timed(s, nsteps, avg_ms, launches, n_out);
+}
+
+int sbp_tile(const sbp_sim *s, int *rows, int *depth)
+{
+    if (!s) return SBP_EINVAL;
+    if (!s->fused_ok) return SBP_ESTATE;
+    if (rows) *rows = s->fused_rows;
+    if (depth) *depth = s->fused_kchunk;
+    return SBP_OK;
 }
 
 int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step)

@@ -107,6 +107,7 @@ def lib():
                 "sbp_half_step_h": (I, [pp, I]),
                 "sbp_half_step_e": (I, [pp, I]),
                 "sbp_autotune": (I, [P, I, C.POINTER(C.c_int), C.POINTER(D)]),
+                "sbp_tile": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
                 "sbp_connect_phase": (I, [P, P, I, D]),
                 "sbp_checkpoint_bytes": (SZ, [P]),
                 "sbp_save": (I, [P, P, SZ]),
@@ -141,7 +142,7 @@ def lib():
 def exported_symbols() -> Sequence[str]:
     return ["sbp_create", "sbp_workspace_bytes", "sbp_create_in", "sbp_connect", "sbp_connect_phase", "sbp_set_field",
             "sbp_get_field", "sbp_add_source", "sbp_add_probe", "sbp_reserve_probes", "sbp_step",
-            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_autotune", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
+            "sbp_step_group", "sbp_half_step_h", "sbp_half_step_e", "sbp_step_timed", "sbp_autotune", "sbp_tile", "sbp_get_probes", "sbp_energy", "sbp_energy_group", "sbp_energy_noalloc", "sbp_energy_series",
             "sbp_sync", "sbp_checkpoint_bytes", "sbp_save", "sbp_load", "sbp_dt", "sbp_step_index", "sbp_destroy", "sbp_strerror",
             "sbp_batch_create", "sbp_batch_add", "sbp_batch_remove", "sbp_batch_remaining", "sbp_batch_step",
             "sbp_batch_size", "sbp_batch_destroy", "sbp_server_create", "sbp_server_submit", "sbp_server_poll",
@@ -305,11 +306,17 @@ class Sim:
         return {k: (ms[q], cnt[q]) for q, k in enumerate(self.KERNELS) if cnt[q]}
 
     def autotune(self, trial_steps=5):
-        """Choose the z-block depth of the one-pass step by timing candidates
-        (state unchanged); returns (depth, ms per step)."""
+        """Choose the tile of the one-pass step (8 or 16 rows, z-block depth) by timing
+        candidates (state unchanged); returns (depth, ms per step); ``tile`` gives the rows."""
         depth, ms = C.c_int(), C.c_double()
         _check(lib().sbp_autotune(self._h, int(trial_steps), C.byref(depth), C.byref(ms)), "sbp_autotune")
         return depth.value, ms.value
+
+    def tile(self):
+        """(rows, depth) of the one-pass step's tile."""
+        rows, depth = C.c_int(), C.c_int()
+        _check(lib().sbp_tile(self._h, C.byref(rows), C.byref(depth)), "sbp_tile")
+        return rows.value, depth.value
 
     def save(self) -> bytes:
         """Checkpoint: the simulation's state as bytes (sbp_save)."""

@@ -45,3 +45,33 @@ def test_autotune_rejects_ineligible():
     with pytest.raises(sbpsat.SbpError):
         s.autotune(1)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [sbpsat.FP32, sbpsat.FP32_FP16STORE])
+@pytest.mark.parametrize("n", [(70, 43, 37), (33, 20, 17), (65, 100, 24)])
+def test_sixteen_row_tiles_bitwise_equal_eight_rows(precision, n, monkeypatch):
+    """The 16-row tile (512 threads, one CTA per SM) computes every node with the same
+    formula as the 8-row tile: fields and probes bit-identical, ragged last rows included."""
+    w = wl.random_box(n, faces=(A, P, M, A, P, M), seed=19, steps=29)
+    monkeypatch.setenv("SBP_FUSED_ROWS", "16")
+    big = sbpsat.from_workload(w, precision=precision)[0]
+    monkeypatch.setenv("SBP_FUSED_ROWS", "8")
+    small = sbpsat.from_workload(w, precision=precision)[0]
+    assert big.tile()[0] == 16 and small.tile()[0] == 8
+    for s in (big, small):
+        s.reserve_probes(29)
+        s.step(29)
+    for c in range(6):
+        assert np.array_equal(big.field(c), small.field(c)), c
+    assert np.array_equal(big.probes(), small.probes())
+    big.close()
+    small.close()
+
+
+def test_autotune_reports_tile():
+    w = wl.random_box((40, 48, 44), seed=3, steps=4)
+    s = sbpsat.from_workload(w)[0]
+    depth, _ = s.autotune(2)
+    rows, d2 = s.tile()
+    assert rows in (8, 16) and d2 == depth
+    s.close()

@@ -22,20 +22,20 @@ def extents(n, c):
     return tuple(n[a] + (1 if ON_PLUS[c][a] else 2) for a in range(3))
 
 
-def fused_nodes(n, depth):
+def fused_nodes(n, depth, rows=FTY):
     """(H nodes, E nodes) the one-pass kernel stores, as lists of (i, j, k) (one entry per store)."""
     nx, ny, nz = n
     tx = (nx - 5 + FTX - 2) // (FTX - 1)
-    ty = (ny - 5 + FTY - 2) // (FTY - 1)
+    ty = (ny - 5 + rows - 2) // (rows - 1)
     tz = (nz - 5 + depth - 1) // depth
     hs, es = [], []
     for bx, by, bz in itertools.product(range(tx), range(ty), range(tz)):
-        x0, y0, k0 = 3 + bx * (FTX - 1), 3 + by * (FTY - 1), 3 + bz * depth
+        x0, y0, k0 = 3 + bx * (FTX - 1), 3 + by * (rows - 1), 3 + bz * depth
         k1 = min(k0 + depth, nz - 2)
-        for w in range(FTY):
+        for w in range(rows):
             j = y0 + w
-            row_e = w < FTY - 1 and j <= ny - 3
-            row_h = j <= ny - 2 and (w < FTY - 1 or j == ny - 2)
+            row_e = w < rows - 1 and j <= ny - 3
+            row_h = j <= ny - 2 and (w < rows - 1 or j == ny - 2)
             for c in range(FTX):
                 i = x0 + c
                 col_h = row_h and i <= nx - 2 and (c < FTX - 1 or i == nx - 2)
@@ -118,9 +118,11 @@ GRIDS = [((8, 8, 8), 8), ((9, 12, 13), 8), ((10, 13, 21), 13), ((68, 12, 17), 8)
          ((70, 19, 33), 13), ((40, 11, 40), 64)]
 
 
+@pytest.mark.parametrize("rows", [8, 16])
 @pytest.mark.parametrize("n, depth", GRIDS)
-def test_every_node_written_once(n, depth):
-    fh, fe = fused_nodes(n, depth)
+def test_every_node_written_once(n, depth, rows):
+    """rows: H rows per one-pass tile (8 or 16 warps)."""
+    fh, fe = fused_nodes(n, depth, rows)
     bh, be = band_nodes(n, 4), band_nodes(n, 3)
     for nodes in (fh, fe, bh, be):                                  # no kernel writes a node twice
         assert len(nodes) == len(set(nodes))
