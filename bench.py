@@ -184,19 +184,21 @@ def device_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str, depth):
+def recorded_traffic(kernel: str, workload: str, depth, rows):
     """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt), if it
-    was taken on the current device code, this workload and (fused kernel) this z-depth."""
+    was taken on the current device code, this workload and (one-pass kernel) this tile:
+    z-block depth and rows."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as f:
-            rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+            table = [l.split() for l in f if l.strip() and not l.startswith("#")]
     except OSError:
         return None
     digest = device_digest()
-    for r in rows:
-        if len(r) >= 5 and r[0] == kernel and r[1] == digest and r[2] == workload and r[3] in ("-", str(depth)):
-            return float(r[4])
+    for r in table:
+        if (len(r) >= 6 and r[0] == kernel and r[1] == digest and r[2] == workload and r[3] in ("-", str(depth))
+                and r[4] in ("-", str(rows))):
+            return float(r[5])
     return None
 
 
@@ -230,9 +232,9 @@ def run_ours(args):
     sim = sbpsat.from_workload(w, stream=stream, precision=prec, flags=flags)[0]
     nk = min(max(args.steps, 100), 400)          # steps of the per-kernel timing leg
     sim.reserve_probes(args.warmup + args.steps + nk + 8)
-    depth = None
     if not args.no_autotune:
-        depth, _ = sim.autotune(20)     # z-block depth of the one-pass step (state unchanged)
+        sim.autotune(20)                # tile of the one-pass step: rows and depth (state unchanged)
+    rows, depth = sim.tile()
 
     with ClockSampler(local) as clk:
         sim.step(args.warmup)
@@ -281,7 +283,7 @@ def run_ours(args):
     ucount, bpc = units[dom]
     mpc = BYTES16[dom] if fp16 else moved[dom]
     achieved = bpc * ucount / (tdom * 1e-3) / 1e9
-    traffic = recorded_traffic(dom, w.name, depth)
+    traffic = recorded_traffic(dom, w.name, depth, rows)
     launches_per_step = sum(c for _, c in times.values()) / nk
     sim.close()
 
@@ -332,7 +334,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": faces,
                        "cfl": w.cfl, "precision": "FP32 arithmetic, FP16 storage" if fp16 else "FP32",
-                       "parallelism": f"replicas x{world}", "z_block_depth": depth,
+                       "parallelism": f"replicas x{world}", "z_block_depth": depth, "tile_rows": rows,
                        "scheme": "SBP-SAT" if args.scheme == "sbp" else "FDTD (Yee) comparator",
                        "l2": "inputs_larger_than_l2 (working set %.0f MB)" % (cells * (28 if fp16 else 52) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,

@@ -45,6 +45,7 @@ def _check(sims, blocks, tol, ptol):
     perr = parity.probe_error(sims, blocks)
     for s in sims:
         s.close()
+    print("relative L2 error per field (E, H) per block:", errs, "probe error:", perr)
     for e in errs:
         assert max(e) < tol, errs
     assert perr < ptol, perr
@@ -99,6 +100,7 @@ def test_two_block_interface_full_size_full_3000_steps():
                                           for c in comps)))
                 norms.append(math.sqrt(sum(float(np.sum(b.field(c) ** 2)) for c in comps)))
         peak = norms if peak is None else [max(a, b) for a, b in zip(peak, norms)]
+        print(f"step {done}: error {errs}, norm {norms}, peak {peak}")
         for e, pk in zip(errs, peak):
             assert e <= FP32_TOL * pk, (done, errs, peak)
         abs_at.append(errs)

@@ -114,7 +114,7 @@ def _counts(n, comps, written):
     return res
 
 
-GRIDS = [((8, 8, 8), 8), ((9, 12, 13), 8), ((10, 13, 21), 13), ((68, 12, 17), 8), ((69, 20, 9), 8),
+GRIDS = [((66, 9, 9), 8), ((67, 9, 10), 8), ((128, 9, 9), 16), ((129, 10, 9), 8), ((8, 8, 8), 8), ((9, 12, 13), 8), ((10, 13, 21), 13), ((68, 12, 17), 8), ((69, 20, 9), 8),
          ((70, 19, 33), 13), ((40, 11, 40), 64)]
 
 
