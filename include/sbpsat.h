@@ -226,8 +226,10 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
  * the depth and its time; sbp_tile reports the rows.  Synchronises the
  * stream.  Errors: SBP_EINVAL, SBP_ESTATE (the grid does not run the
  * one-pass step, or has an interface to another block), SBP_ECUDA,
- * SBP_ETIMEOUT.  Batch members run 8-row tiles (a member tuned to 16 rows
- * returns to 8 when it joins a batch). */
+ * SBP_ETIMEOUT.  A batch runs all its members on one tile height: 16 rows
+ * when every member has at least 20 cells along y and the batch steps with
+ * three launches per step, else 8 (the environment variable SBP_FUSED_ROWS=8
+ * forces 8); a member's own tile is changed to it when the batch is built. */
 int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step);
 /* Tile of the one-pass step: H rows per CTA (8 or 16) and z-block depth.
  * SBP_ESTATE if the simulation does not run the one-pass step. */

@@ -737,8 +737,11 @@ __device__ __forceinline__ bool batch_state(const BatchGrid &g, int offset, long
     return true;
 }
 
-__global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_batched(const BatchGrid *G, const int *pre, int n,
-                                                                                  int offset)
+// R: tile rows of every member's one-pass tiles (8, or 16 when every member
+// has a full 16-row tile).
+template <int R>
+__global__ void __launch_bounds__(R * 32, R >= 16 ? 1 : (kStages <= 3 ? 3 : 2))
+    fused_batched(const BatchGrid *G, const int *pre, int n, int offset)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int g = find_slot(pre, n, blockIdx.x);
@@ -748,8 +751,8 @@ __global__ void __launch_bounds__(kFTY * 32, kStages <= 3 ? 3 : 2) fused_batched
     if (!batch_state(B, offset, step, par)) return;
     const int local = blockIdx.x - pre[g];
     const int tx = B.tiles[0], ty = B.tiles[1];
-    fused_body<true, float>(B.maps[par], B.fp[par], step, step - B.probe_base, local % tx, (local / tx) % ty,
-                            local / (tx * ty), smem_raw);
+    fused_body<true, float, R>(B.maps[par], B.fp[par], step, step - B.probe_base, local % tx, (local / tx) % ty,
+                               local / (tx * ty), smem_raw);
 }
 
 __global__ void __launch_bounds__(256) band_h_batched(const BatchGrid *G, const int *pre, int n, int offset)

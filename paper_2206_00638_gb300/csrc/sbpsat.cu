@@ -628,7 +628,8 @@ int set_fused_smem_attr()
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float, 16>, attr, sbp::FusedGeom<float, 16>::kSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half, 16>, attr, sbp::FusedGeom<__half, 16>::kSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half, 16>, attr, sbp::FusedGeom<__half, 16>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched, attr, sbp::kFusedSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched<8>, attr, sbp::FusedGeom<float, 8>::kSmem));
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched<16>, attr, sbp::FusedGeom<float, 16>::kSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::persistent_batched, attr, sbp::kFusedSmem));
         done[dev] = true;
     }
@@ -1097,6 +1098,7 @@ struct sbp_batch {
     long long *d_counters = nullptr;
     int cap = 0;
     int nf = 0, nh = 0, ne = 0;         // CTAs per launch
+    int rows = sbp::kFTY;               // tile rows of the per-step one-pass launch (8 or 16)
     int ni = 0;                         // persistent-kernel items per step
     sbp::BatchGrid *h_grids = nullptr;  // pinned staging of the uploads
     int *h_pre = nullptr;
@@ -1159,13 +1161,22 @@ int batch_rebuild(sbp_batch *b)
     long long *cnt = b->h_counters;
     std::memset(pre, 0, sizeof(int) * 4 * (b->cap + 1));
     int *pf = pre, *ph = pre + (b->cap + 1), *pe = pre + 2 * (b->cap + 1), *pi = pre + 3 * (b->cap + 1);
+    // 16-row tiles (one 512-thread CTA per SM, which leaves room for the band
+    // kernels beside it) when every member has a full one, and the per-step
+    // path runs; else 8 rows (the persistent kernel always runs 8)
+    int rows = b->persistent ? sbp::kFTY : 16;
+    if (const char *env = std::getenv("SBP_FUSED_ROWS"))
+        if (std::atoi(env) == 8) rows = sbp::kFTY;
+    for (int g = 0; g < n; g++)
+        if (b->m[g].s->n[1] - 5 < 15) rows = sbp::kFTY;
+    b->rows = rows;
     for (int g = 0; g < n; g++) {
         sbp_sim *s = b->m[g].s;
         sbp::BatchGrid &G = hg[g];
         std::memset(static_cast<void *>(&G), 0, sizeof(G));
-        // the batched kernels run 8-row tiles: a member tuned to another tile
-        // height returns to 8 rows (its TMA boxes are re-encoded)
-        if (s->fused_rows != sbp::kFTY && (rc = set_tile(s, sbp::kFTY, s->fused_kchunk))) return rc;
+        // every member runs the batch's tile height (its TMA boxes are re-encoded
+        // when it differs from the member's own)
+        if (s->fused_rows != rows && (rc = set_tile(s, rows, s->fused_kchunk))) return rc;
         for (int c = 0; c < 2; c++) {
             G.maps[c] = s->maps[c];
             if ((rc = make_fused_params(s, c, G.fp[c]))) return rc;
@@ -1247,8 +1258,12 @@ int batch_launch_chunk(sbp_batch *b, long long K)
         // which includes the first interior H layer), joined before the next step
         for (long long o = 0; o < K; o++) {
             SBP_CUDA(cudaEventRecord(b->ev_fork, b->stream));
-            if (b->nf > 0)
-                sbp::fused_batched<<<b->nf, sbp::kFTY * 32, sbp::kFusedSmem, b->stream>>>(b->d_grids, pf, n, (int)o);
+            if (b->nf > 0 && b->rows == 16)
+                sbp::fused_batched<16><<<b->nf, 16 * 32, sbp::FusedGeom<float, 16>::kSmem, b->stream>>>(
+                    b->d_grids, pf, n, (int)o);
+            else if (b->nf > 0)
+                sbp::fused_batched<8><<<b->nf, 8 * 32, sbp::FusedGeom<float, 8>::kSmem, b->stream>>>(
+                    b->d_grids, pf, n, (int)o);
             SBP_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
             if (b->nh > 0) sbp::band_h_batched<<<b->nh, 256, 0, b->side>>>(b->d_grids, ph, n, (int)o);
             if (b->ne > 0) sbp::band_e_batched<<<b->ne, 256, 0, b->side>>>(b->d_grids, pe, n, (int)o);
