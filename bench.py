@@ -55,9 +55,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", choices=["dielectric", "mixed", "serve"], default="mixed",
+    ap.add_argument("--workload", choices=["dielectric", "mixed", "serve", "twoblock", "cavity"], default="mixed",
                     help="mixed: the N^3 block with PMC x, PEC y, absorbing z faces and four dielectric "
-                         "spheres (default); dielectric: the N^3 dielectric cube; serve: the request stream alone")
+                         "spheres (default); dielectric: the N^3 dielectric cube; serve: the request stream alone; "
+                         "twoblock: two 192x192x96 blocks joined by the interface SAT; cavity: the 20x16x12 PEC "
+                         "cavity in FP64")
     ap.add_argument("--no-serve", action="store_true", help="leave the serving stream out of the line")
     ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32",
                     help="fp16: FP32 arithmetic with FP16 field storage")
@@ -529,6 +531,54 @@ def serve_stream(args):
     }
 
 
+def run_blocks(args):
+    """Throughput of the other block workloads, device-timed like the default line: the two
+    192x192x96 blocks joined on z by the interface SAT (FP32, stepped as a group) and the PEC
+    cavity (20x16x12, FP64, the in-place path)."""
+    import torch
+
+    from paper_2206_00638_gb300 import sbpsat
+    from paper_2206_00638_gb300 import workloads as wl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if args.workload == "twoblock":
+        w, prec = wl.two_block(steps=args.steps), sbpsat.FP32
+    else:
+        w, prec = wl.cavity(steps=args.steps), sbpsat.FP64
+    stream = torch.cuda.current_stream()
+    sims = sbpsat.from_workload(w, stream=stream, precision=prec)
+    for s in sims:
+        s.reserve_probes(args.warmup + args.steps + 8)
+    sbpsat.step_group(sims, args.warmup)
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        clk.wait_for_sample(time.perf_counter())
+        t0 = time.perf_counter()
+        start.record(stream)
+        sbpsat.step_group(sims, args.steps)
+        stop.record(stream)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        clk.wait_for_sample(t1)
+        clocks = clk.summary(t0, t1)
+    ms = start.elapsed_time(stop)
+    cells = w.cells()
+    for s in sims:
+        s.close()
+    line = {
+        "metric": "Gcell-updates/s", "value": cells * args.steps / (ms * 1e-3) / 1e9, "unit": "Gcell-updates/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == sbpsat.FP64 else "f32", "data": "synthetic",
+        "config": {"workload": w.name, "cells": cells, "blocks": len(sims),
+                   "precision": "FP64" if prec == sbpsat.FP64 else "FP32"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+
+
 def run_serve(args):
     """The serving stream alone, as its own JSON line."""
     import torch
@@ -550,6 +600,8 @@ def main():
         run_reference(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload in ("twoblock", "cavity"):
+        run_blocks(args)
     else:
         run_ours(args)
 
