@@ -186,10 +186,10 @@ def device_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str, depth, rows):
+def recorded_traffic(kernel: str, workload: str, depth, rows, width):
     """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt), if it
     was taken on the current device code, this workload and (one-pass kernel) this tile:
-    z-block depth and rows."""
+    z-block depth, rows and width."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as f:
@@ -198,9 +198,9 @@ def recorded_traffic(kernel: str, workload: str, depth, rows):
         return None
     digest = device_digest()
     for r in table:
-        if (len(r) >= 6 and r[0] == kernel and r[1] == digest and r[2] == workload and r[3] in ("-", str(depth))
-                and r[4] in ("-", str(rows))):
-            return float(r[5])
+        if (len(r) >= 7 and r[0] == kernel and r[1] == digest and r[2] == workload and r[3] in ("-", str(depth))
+                and r[4] in ("-", str(rows)) and r[5] in ("-", str(width))):
+            return float(r[6])
     return None
 
 
@@ -236,7 +236,7 @@ def run_ours(args):
     sim.reserve_probes(args.warmup + args.steps + nk + 8)
     if not args.no_autotune:
         sim.autotune(20)                # tile of the one-pass step: rows and depth (state unchanged)
-    rows, depth = sim.tile()
+    rows, depth, width = sim.tile()
 
     with ClockSampler(local) as clk:
         sim.step(args.warmup)
@@ -285,7 +285,7 @@ def run_ours(args):
     ucount, bpc = units[dom]
     mpc = BYTES16[dom] if fp16 else moved[dom]
     achieved = bpc * ucount / (tdom * 1e-3) / 1e9
-    traffic = recorded_traffic(dom, w.name, depth, rows)
+    traffic = recorded_traffic(dom, w.name, depth, rows, width)
     launches_per_step = sum(c for _, c in times.values()) / nk
     sim.close()
 
@@ -337,6 +337,7 @@ def run_ours(args):
             "config": {"workload": w.name, "cells": cells, "h_m": spec.h[0], "faces": faces,
                        "cfl": w.cfl, "precision": "FP32 arithmetic, FP16 storage" if fp16 else "FP32",
                        "parallelism": f"replicas x{world}", "z_block_depth": depth, "tile_rows": rows,
+                       "tile_width": width,
                        "scheme": "SBP-SAT" if args.scheme == "sbp" else "FDTD (Yee) comparator",
                        "l2": "inputs_larger_than_l2 (working set %.0f MB)" % (cells * (28 if fp16 else 52) / 1e6)},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,

@@ -212,9 +212,10 @@ int sbp_half_step_e(sbp_sim **sims, int nsims);
 int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches, int n_out);
 
 /* Autotuner of the one-pass interior step (no counterpart in the paper, whose
- * own loops are CPU code): times every candidate tile -- 8 or 16 H rows per
- * CTA (16 when the grid has at least 15 interior rows) times z-block depths of
- * 8..256 planes up to the grid's interior depth -- with trial_steps (>= 1)
+ * own loops are CPU code): times every candidate tile -- 64 H columns by 8 or
+ * 16 rows, or 128 columns by 8 or 12 rows (a height or width only when the
+ * grid's interior holds one full tile of it) -- times z-block depths of
+ * 8..256 planes up to the grid's interior depth, with trial_steps (>= 1)
  * device steps each, on the simulation's stream, and keeps the fastest.  The
  * trial steps are not committed: they write the spare field set and the
  * current probe slot, which the next step overwrites, so the simulation's
@@ -223,17 +224,19 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
  * choice is remembered for this grid shape and precision and applied to
  * simulations created later in the process (and written to the file named by
  * SBP_TUNE_CACHE, if set).  *chosen_depth and *ms_per_step (optional) receive
- * the depth and its time; sbp_tile reports the rows.  Synchronises the
+ * the depth and its time; sbp_tile reports the whole tile.  Synchronises the
  * stream.  Errors: SBP_EINVAL, SBP_ESTATE (the grid does not run the
  * one-pass step, or has an interface to another block), SBP_ECUDA,
- * SBP_ETIMEOUT.  A batch runs all its members on one tile height: 16 rows
- * when every member has at least 20 cells along y and the batch steps with
- * three launches per step, else 8 (the environment variable SBP_FUSED_ROWS=8
- * forces 8); a member's own tile is changed to it when the batch is built. */
+ * SBP_ETIMEOUT.  A batch runs all its members on one tile, 64 columns wide:
+ * 16 rows when every member has at least 20 cells along y and the batch steps
+ * with three launches per step, else 8 (the environment variable
+ * SBP_FUSED_ROWS=8 forces 8); a member's own tile is changed to it when the
+ * batch is built. */
 int sbp_autotune(sbp_sim *s, int trial_steps, int *chosen_depth, double *ms_per_step);
-/* Tile of the one-pass step: H rows per CTA (8 or 16) and z-block depth.
- * SBP_ESTATE if the simulation does not run the one-pass step. */
-int sbp_tile(const sbp_sim *s, int *rows, int *depth);
+/* Tile of the one-pass step: H rows per CTA (8, 12 or 16), z-block depth
+ * and H columns per CTA (64 or 128); each pointer may be NULL.  SBP_ESTATE if
+ * the simulation does not run the one-pass step. */
+int sbp_tile(const sbp_sim *s, int *rows, int *depth, int *width);
 
 /* Batches: continuous batching of many simulations.  A batch advances all
  * its member simulations together, one kernel launch per kernel kind per

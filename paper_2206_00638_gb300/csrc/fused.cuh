@@ -11,11 +11,13 @@
 // tile has written it, the new fields go to a second buffer set (ping-pong)
 // and each CTA recomputes the one-node H halo it needs.
 //
-// CTA = 8 warps, tile of H columns x0..x0+63 and rows y0..y0+7 (warp = row,
-// lane = columns x0+L and x0+32+L); E is produced for the inner 63 x 7.  A
-// 4-stage pipeline of 3D TMA tensor copies (one box per field per z-plane,
-// completion on an mbarrier) keeps ~48 KB per CTA in flight; H^{n+1/2} of
-// the current and next plane is exchanged through shared memory.
+// A tile is W H columns x0..x0+W-1 (W = 64 or 128) by R rows y0..y0+R-1.
+// Each row is served by W/64 warps, each lane by two columns of its warp's
+// 64 (x0+g+L and x0+g+32+L); E is produced for the inner (W-1) x (R-1).
+// Wider tiles read longer contiguous row segments and fewer halo columns per
+// cell.  A 4-stage pipeline of 3D TMA tensor copies (one box per field per
+// z-plane, completion on an mbarrier) keeps three planes in flight; H^{n+1/2}
+// of the current and next plane is exchanged through shared memory.
 //
 // band_h / band_e evaluate the remaining nodes (the three boundary layers of
 // each axis, closure rows and SAT penalties) with the general-path code of
@@ -27,8 +29,8 @@
 
 namespace sbp {
 
-constexpr int kFTX = 64;                 // H footprint width
-constexpr int kFTY = 8;                  // H footprint rows (= warps) of the default tile and of batches
+constexpr int kFTX = 64;                 // H footprint width of the default tile and of batches
+constexpr int kFTY = 8;                  // H footprint rows of the default tile and of batches
 #ifndef SBP_FUSED_STAGES
 #define SBP_FUSED_STAGES 4
 #endif
@@ -38,18 +40,20 @@ constexpr unsigned kWaitLimit = 1u << 22;
 constexpr int round128(int bytes) { return (bytes + 127) / 128 * 128; }
 
 // Shared-memory geometry of one pipeline stage for field storage type S and
-// a tile of R H rows (R warps; E is produced on the inner R-1 rows).  A TMA
-// box starts at an x that is a multiple of 16 bytes (4 FP32 or 8 FP16
-// elements) at or below x0-1 and spans the 64 columns after it: kBX columns.
+// a tile of R H rows by W columns (E is produced on the inner R-1 rows).  A
+// TMA box starts at an x that is a multiple of 16 bytes (4 FP32 or 8 FP16
+// elements) at or below x0-1 and spans the W columns after it: kBX columns.
 // The E box holds rows y0-1 .. y0+R-1, the H and eps boxes rows y0 .. y0+R-1.
 // The eps box (always FP32) uses the same start and width.
-template <typename S, int R = kFTY>
+template <typename S, int R = kFTY, int W = kFTX>
 struct FusedGeom {
+    static_assert(W == 64 || W == 128, "tile width");
+    static constexpr int kWarps = R * (W / 64);
     static constexpr int kERows = R + 1;
     static constexpr int kHRows = R;
-    static constexpr int kHbufFloats = 2 * 3 * R * kFTX;   // H^{n+1/2} of two planes
+    static constexpr int kHbufFloats = 2 * 3 * R * W;      // H^{n+1/2} of two planes
     static constexpr int kAlign = 16 / (int)sizeof(S);
-    static constexpr int kBX = kFTX + kAlign;
+    static constexpr int kBX = W + kAlign;
     static constexpr int kEBytes = round128(kERows * kBX * (int)sizeof(S));   // one E box slot
     static constexpr int kHBytes = round128(kHRows * kBX * (int)sizeof(S));   // one H box slot
     static constexpr int kPBytes = round128(kHRows * kBX * 4);                // the eps box slot
@@ -139,11 +143,11 @@ struct FusedMaps {
     CUtensorMap e[3], h[3], eps;
 };
 
-template <typename S, int R>
+template <typename S, int R, int W>
 __device__ __forceinline__ void issue_plane(const FusedMaps &m, unsigned char *stage, uint64_t *bar, int xb, int y0,
                                             int plane)
 {
-    using Gm = FusedGeom<S, R>;
+    using Gm = FusedGeom<S, R, W>;
     mbar_expect_tx(bar, Gm::kTxBytes);
 #pragma unroll
     for (int f = 0; f < 3; ++f) tma_load_3d(stage + f * Gm::kEBytes, &m.e[f], xb, y0 - 1, plane, bar);
@@ -154,12 +158,14 @@ __device__ __forceinline__ void issue_plane(const FusedMaps &m, unsigned char *s
 
 // One CTA of the one-pass interior step: tile (bx, by) in x/y, z-chunk bz,
 // time step `step` (J is evaluated at t^{step+1/2}), probe sample `pslot`.
-template <bool SRC, typename S, int R = kFTY>
+template <bool SRC, typename S, int R = kFTY, int W = kFTX>
 __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedParamsT<S> &p, long long step,
                                            long long pslot, int bx, int by, int bz, unsigned char *smem)
 {
-    using Gm = FusedGeom<S, R>;
-    constexpr int kFTY = R;                        // tile rows (= warps) of this instantiation
+    using Gm = FusedGeom<S, R, W>;
+    constexpr int kFTY = R;                        // tile rows of this instantiation
+    constexpr int kFTX = W;                        // tile columns
+    constexpr int kGroups = W / 64;                // warps per row
     constexpr int kBX = Gm::kBX;
     float *hbuf = reinterpret_cast<float *>(smem + kStages * Gm::kStageBytes);
     uint64_t *bar = reinterpret_cast<uint64_t *>(hbuf + Gm::kHbufFloats);
@@ -172,7 +178,9 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         return reinterpret_cast<const float *>(smem + st * Gm::kStageBytes + 3 * Gm::kEBytes + 3 * Gm::kHBytes);
     };
 
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // warp wid serves row w, columns cg .. cg+63 of the tile
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int w = wid / kGroups, cg = (wid % kGroups) * 64;
     const int nx = p.n[0], ny = p.n[1], nz = p.n[2];
     const int x0 = 3 + bx * (kFTX - 1);
     const int y0 = 3 + by * (kFTY - 1);
@@ -191,13 +199,13 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     int issued = 0;                                   // planes issued (thread 0's count)
     if (threadIdx.x == 0 && !p.test_stall)
         for (; issued < kStages && issued < nplanes; ++issued)
-            issue_plane<S, R>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
+            issue_plane<S, R, W>(maps, smem + issued * Gm::kStageBytes, &bar[issued], xb, y0, k0 - 1 + issued);
     // J(t^{n+1/2}) of every source is the same at each node it reaches, so
     // warp 1 evaluates it once per CTA (FP64 waveform, rounded to FP32 once)
     // while the first planes load; it is first read after the barrier below.
     static_assert(kMaxSources <= 32, "one lane of warp 1 per source");
     __shared__ float sJ[kMaxSources];
-    if (SRC && w == 1 && lane < p.nsrc) {
+    if (SRC && wid == 1 && lane < p.nsrc) {
         const Src &Sr = p.src[lane];
         const double t_half = ((double)step + 0.5) * p.dt;
         sJ[lane] = (float)(Sr.amp * waveform(Sr.wf, t_half, Sr.tw, Sr.t0, Sr.f));
@@ -208,7 +216,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     unsigned smask[2] = {0u, 0u};
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int i = x0 + lane + 32 * h;
+        const int i = x0 + cg + lane + 32 * h;
         for (int q = 0; q < p.nprb; ++q)
             if (p.prb[q].i == i && p.prb[q].j == j) pmask[h] |= 1ull << q;
         if (SRC)
@@ -220,13 +228,13 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     // per column: stores owned (H) / produced (E) by this thread, and the
     // column's offset within a plane
     bool colH[2], colE[2];
-    long long obase[2];
+    int obase[2];                                     // j * sy + i (a plane has fewer than 2^31 elements)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int c = lane + 32 * h, i = x0 + c;
+        const int c = cg + lane + 32 * h, i = x0 + c;
         colH[h] = rowH && i <= nx - 2 && (c < kFTX - 1 || i == nx - 2);
         colE[h] = rowE && c < kFTX - 1 && i <= nx - 3;
-        obase[h] = (long long)j * p.sy + i;
+        obase[h] = j * (int)p.sy + i;
     }
     const Coef<float> Bx = p.B[0], By = p.B[1], Bz = p.B[2];
     const Coef<float> Ax = p.A[0], Ay = p.A[1], Az = p.A[2];
@@ -240,7 +248,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     if (nplanes > 0) { ok = mbar_wait_bounded(&bar[0], 0, p.wait_limit); waited = 1; }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int re = (w + 1) * kBX + cx0 + lane + 32 * h;
+        const int re = (w + 1) * kBX + cx0 + cg + lane + 32 * h;
 #pragma unroll
         for (int f = 0; f < 3; ++f) { ec[h][f] = ld_s(slotE(0, f) + re); hc[h][f] = 0.f; }
 #pragma unroll
@@ -249,7 +257,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
     fence_generic_to_async();                         // the E carries of plane k0-1
     if (__syncthreads_or(!ok)) aborted = true;
     if (!aborted && threadIdx.x == 0 && kStages < nplanes) {   // plane k0-1 is in registers now
-        issue_plane<S, R>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
+        issue_plane<S, R, W>(maps, smem, &bar[0], xb, y0, k0 - 1 + kStages);
         ++issued;
     }
 #pragma unroll(sizeof(S) == 4 ? 2 : 1)   // two planes per iteration with FP32 storage (faster there, slower with FP16)
@@ -272,9 +280,15 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             for (int b = 0; b < p.nsrc; ++b)
                 if (p.src[b].k < 0 || p.src[b].k == pl) splane |= 1u << b;
 
+        // output rows of plane q (H) and pl (E): a base shared by the CTA plus the
+        // thread's 32-bit offset within the plane
+        S *const oH0 = p.out[3] + (long long)q * p.sz, *const oH1 = p.out[4] + (long long)q * p.sz,
+                 *const oH2 = p.out[5] + (long long)q * p.sz;
+        S *const oE0 = p.out[0] + (long long)pl * p.sz, *const oE1 = p.out[1] + (long long)pl * p.sz,
+                 *const oE2 = p.out[2] + (long long)pl * p.sz;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int c = lane + 32 * h;
+            const int c = cg + lane + 32 * h;
             const int cc = cx0 + c;
             // ---- H^{n+1/2} at (i, j, q) --------------------------------------
             const int re = (w + 1) * kBX + cc;            // E slot row of j
@@ -295,10 +309,9 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             Hq[(1 * kFTY + w) * kFTX + c] = hy;
             Hq[(2 * kFTY + w) * kFTX + c] = hz;
             if (colH[h] && (q < k1 || q == nz - 2)) {
-                const long long o = (long long)q * p.sz + obase[h];
-                st_s(p.out[3] + o, hx);
-                st_s(p.out[4] + o, hy);
-                st_s(p.out[5] + o, hz);
+                st_s(oH0 + obase[h], hx);
+                st_s(oH1 + obase[h], hy);
+                st_s(oH2 + obase[h], hz);
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
@@ -349,10 +362,9 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                 const float ex = quant<S>(ec[h][0] + scaled_increment(ax, sx));
                 const float ey = quant<S>(ec[h][1] + scaled_increment(ay, sy));
                 const float ez = quant<S>(ec[h][2] + scaled_increment(az, sz));
-                const long long o = (long long)pl * p.sz + obase[h];
-                st_s(p.out[0] + o, ex);
-                st_s(p.out[1] + o, ey);
-                st_s(p.out[2] + o, ez);
+                st_s(oE0 + obase[h], ex);
+                st_s(oE1 + obase[h], ey);
+                st_s(oE2 + obase[h], ez);
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
@@ -376,7 +388,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         if (threadIdx.x == 0) {
             const int nxt = q + kStages;
             if (nxt <= k1) {
-                issue_plane<S, R>(maps, smem + sq * Gm::kStageBytes, &bar[sq], xb, y0, nxt);
+                issue_plane<S, R, W>(maps, smem + sq * Gm::kStageBytes, &bar[sq], xb, y0, nxt);
                 ++issued;
             }
         }
@@ -398,12 +410,13 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
         for (int s = 0; s < kStages; ++s) mbar_inval(&bar[s]);
 }
 
-template <bool SRC, typename S, int R>
-__global__ void __launch_bounds__(R * 32, R >= 16 ? 1 : (kStages <= 3 ? 3 : 2))
+template <bool SRC, typename S, int R, int W>
+__global__ void __launch_bounds__(FusedGeom<S, R, W>::kWarps * 32,
+                                  FusedGeom<S, R, W>::kWarps >= 16 ? 1 : (kStages <= 3 ? 3 : 2))
     fused_interior(const __grid_constant__ FusedMaps maps, const FusedParamsT<S> p)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    fused_body<SRC, S, R>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
+    fused_body<SRC, S, R, W>(maps, p, p.step, p.probe_slot, blockIdx.x, blockIdx.y, blockIdx.z, smem_raw);
 }
 
 // ---------------------------------------------------------------------------

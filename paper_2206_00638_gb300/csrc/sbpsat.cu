@@ -96,7 +96,8 @@ struct sbp_sim {
     int *error_flag = nullptr;            // device flag raised by a pipeline wait that gave up
     sbp::FusedMaps maps[2];               // TMA tensor maps reading set 0 / set 1
     int fused_kchunk = 32;
-    int fused_rows = sbp::kFTY;           // tile rows of the one-pass step (8 or 16)
+    int fused_rows = sbp::kFTY;           // tile rows of the one-pass step (tile_valid)
+    int fused_width = sbp::kFTX;          // tile columns of the one-pass step (64 or 128)
     dim3 fused_grid;
     bool async_setup = false;             // caller keeps host inputs alive: no stream syncs in setup
     cudaStream_t side = nullptr;          // band_h runs here, concurrently with fused_interior
@@ -138,14 +139,24 @@ struct Layout {
     bool fused;
     int fused_kchunk;
     int fused_rows;
+    int fused_width;
     dim3 fused_grid;
     size_t total;
 };
 
-// Grid of the one-pass step for tiles of `rows` H rows and z-blocks of `depth` planes.
-dim3 fused_dims(const int n[3], int rows, int depth)
+// One-pass tiles: 64 columns by 8 or 16 rows (8 or 16 warps), or 128 columns
+// by 8 or 12 rows (16 or 24 warps, two per row); the larger ones use most of
+// an SM's shared memory.
+bool tile_valid(int width, int rows)
 {
-    const int tx = (n[0] - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
+    return (width == 64 && (rows == 8 || rows == 16)) || (width == 128 && (rows == 8 || rows == 12));
+}
+
+// Grid of the one-pass step for tiles of `width` x `rows` H nodes and z-blocks
+// of `depth` planes.
+dim3 fused_dims(const int n[3], int width, int rows, int depth)
+{
+    const int tx = (n[0] - 5 + width - 2) / (width - 1);
     const int ty = (n[1] - 5 + rows - 2) / (rows - 1);
     return dim3(tx, ty, (n[2] - 5 + depth - 1) / depth);
 }
@@ -180,15 +191,18 @@ bool desc_valid(const sbp_grid_desc *d)
     return true;
 }
 
-// tiles (z-block depth, rows) chosen by sbp_autotune, per grid shape and precision
+// tiles chosen by sbp_autotune, per grid shape and precision
+struct TileChoice {
+    int depth = 0, rows = 0, width = 0;    // depth 0: none recorded
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tuned;   // (depth, rows)
+std::map<std::tuple<int, int, int, int>, TileChoice> g_tuned;
 bool g_tune_file_read = false;
 
 // Optional persistence: SBP_TUNE_CACHE names a file of JSON lines
-// {"nx": .., "ny": .., "nz": .., "precision": .., "depth": .., "rows": ..}
-// (a line without "rows" means 8), read once and appended to by every
-// tuning.  Caller holds g_tune_mu.
+// {"nx": .., "ny": .., "nz": .., "precision": .., "depth": .., "rows": .., "width": ..}
+// (a line without "rows" means 8, without "width" 64), read once and appended
+// to by every tuning.  Caller holds g_tune_mu.
 void read_tune_file()
 {
     if (g_tune_file_read) return;
@@ -199,33 +213,40 @@ void read_tune_file()
     if (!f) return;
     char line[256];
     while (std::fgets(line, sizeof(line), f)) {
-        int nx, ny, nz, prec, depth, rows = sbp::kFTY;
-        const int got = std::sscanf(line, " {\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d, \"rows\": %d}",
-                                    &nx, &ny, &nz, &prec, &depth, &rows);
-        if (got >= 5 && depth > 0 && (rows == 8 || rows == 16))
-            g_tuned[std::make_tuple(nx, ny, nz, prec)] = std::make_pair(depth, rows);
+        int nx, ny, nz, prec, depth, rows = sbp::kFTY, width = sbp::kFTX;
+        const int got = std::sscanf(line,
+                                    " {\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d, "
+                                    "\"rows\": %d, \"width\": %d}",
+                                    &nx, &ny, &nz, &prec, &depth, &rows, &width);
+        if (got >= 5 && depth > 0 && tile_valid(width, rows)) {
+            TileChoice t;
+            t.depth = depth; t.rows = rows; t.width = width;
+            g_tuned[std::make_tuple(nx, ny, nz, prec)] = t;
+        }
     }
     std::fclose(f);
 }
 
-void append_tune_file(int nx, int ny, int nz, int prec, int depth, int rows)
+void append_tune_file(int nx, int ny, int nz, int prec, const TileChoice &t)
 {
     const char *path = std::getenv("SBP_TUNE_CACHE");
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d, \"rows\": %d}\n", nx, ny,
-                 nz, prec, depth, rows);
+    std::fprintf(f,
+                 "{\"nx\": %d, \"ny\": %d, \"nz\": %d, \"precision\": %d, \"depth\": %d, \"rows\": %d, "
+                 "\"width\": %d}\n",
+                 nx, ny, nz, prec, t.depth, t.rows, t.width);
     std::fclose(f);
 }
 
-// (depth, rows) chosen by sbp_autotune for this shape and precision, or (0, 0).
-std::pair<int, int> tuned_tile(const sbp_grid_desc *d)
+// Tile chosen by sbp_autotune for this shape and precision (depth 0 if none).
+TileChoice tuned_tile(const sbp_grid_desc *d)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     read_tune_file();
     auto it = g_tuned.find(std::make_tuple(d->nx, d->ny, d->nz, d->precision));
-    return it == g_tuned.end() ? std::make_pair(0, 0) : it->second;
+    return it == g_tuned.end() ? TileChoice() : it->second;
 }
 
 Layout make_layout(const sbp_grid_desc *d)
@@ -252,29 +273,40 @@ Layout make_layout(const sbp_grid_desc *d)
     L.grid = dim3(gx, gy, gz);
     L.npartials = (long long)gx * gy * gz;
     L.partial_bytes = round_up((size_t)L.npartials * sizeof(double), 256);
+    // (the one-pass kernel addresses a plane with 32-bit offsets)
     L.fused = d->precision != SBP_FP64 && !d->mu_r && d->nx >= 8 && d->ny >= 8 && d->nz >= 8 &&
-              !std::getenv("SBP_NO_FUSED");
+              L.sz < (1ll << 31) && !std::getenv("SBP_NO_FUSED");
+    L.fused_kchunk = 32;
+    L.fused_rows = sbp::kFTY;
+    L.fused_width = sbp::kFTX;
+    L.fused_grid = dim3(1, 1, 1);
     if (L.fused) {
         const int tx = (d->nx - 5 + sbp::kFTX - 2) / (sbp::kFTX - 1);
         const int ty = (d->ny - 5 + sbp::kFTY - 2) / (sbp::kFTY - 1);
         const long long target = 4ll * 2 * 152;        // about four waves of two CTAs per SM
         const long long chunks = std::max(1ll, (target + (long long)tx * ty - 1) / ((long long)tx * ty));
         int kcf = (int)std::max(8ll, ((long long)(d->nz - 5) + chunks - 1) / chunks);
-        const std::pair<int, int> tt = tuned_tile(d);
-        int rows = sbp::kFTY;
-        if (tt.first) { kcf = tt.first; rows = tt.second; }
+        const TileChoice tt = tuned_tile(d);
+        int rows = sbp::kFTY, width = sbp::kFTX;
+        if (tt.depth) { kcf = tt.depth; rows = tt.rows; width = tt.width; }
         if (const char *env = std::getenv("SBP_FUSED_KCHUNK")) {
             const int v = std::atoi(env);
             if (v > 0) kcf = v;
         }
+        if (const char *env = std::getenv("SBP_FUSED_WIDTH")) {
+            const int v = std::atoi(env);
+            if (v == 64 || v == 128) width = v;
+        }
         if (const char *env = std::getenv("SBP_FUSED_ROWS")) {
             const int v = std::atoi(env);
-            if (v == 8 || v == 16) rows = v;
+            if (tile_valid(width, v)) rows = v;
         }
+        if (!tile_valid(width, rows)) rows = sbp::kFTY;
         L.fused_kchunk = kcf;
         L.fused_rows = rows;
+        L.fused_width = width;
         const int nn[3] = {d->nx, d->ny, d->nz};
-        L.fused_grid = fused_dims(nn, rows, kcf);
+        L.fused_grid = fused_dims(nn, width, rows, kcf);
         (void)tx;
         (void)ty;
     }
@@ -336,12 +368,14 @@ int encode_one(CUtensorMap *m, void *base, const sbp_sim *s, int rows, int esize
     return r == CUDA_SUCCESS ? SBP_OK : SBP_ECUDA;
 }
 
-// TMA maps of both field sets for the current tile rows: E boxes of rows+1
-// rows (y0-1 .. y0+rows-1), H and eps boxes of rows rows.
+// TMA maps of both field sets for the current tile: E boxes of rows+1 rows
+// (y0-1 .. y0+rows-1), H and eps boxes of rows rows, all width + 16 bytes wide.
 int encode_maps(sbp_sim *s)
 {
     const int es = (int)s->esize;
-    const int bx = es == 2 ? sbp::FusedGeom<__half>::kBX : sbp::FusedGeom<float>::kBX;
+    const bool wide = s->fused_width == 128;
+    const int bx = es == 2 ? (wide ? sbp::FusedGeom<__half, 8, 128>::kBX : sbp::FusedGeom<__half>::kBX)
+                           : (wide ? sbp::FusedGeom<float, 8, 128>::kBX : sbp::FusedGeom<float>::kBX);
     const int rows = s->fused_rows;
     for (int set = 0; set < 2; set++) {
         for (int f = 0; f < 3; f++) {
@@ -383,6 +417,7 @@ int setup(sbp_sim *s, const sbp_grid_desc *d, const Layout &L, char *ws)
     s->fused_ok = L.fused;
     s->fused_kchunk = L.fused_kchunk;
     s->fused_rows = L.fused_rows;
+    s->fused_width = L.fused_width;
     s->fused_grid = L.fused_grid;
     char *p = ws;
     for (int set = 0; set < (L.fused ? 2 : 1); set++)
@@ -620,20 +655,34 @@ int set_fused_smem_attr()
     cudaGetDevice(&dev);
     if (dev >= 0 && dev < 64 && !done[dev]) {
         const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, float, 8>, attr, sbp::FusedGeom<float, 8>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float, 8>, attr, sbp::FusedGeom<float, 8>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half, 8>, attr, sbp::FusedGeom<__half, 8>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half, 8>, attr, sbp::FusedGeom<__half, 8>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, float, 16>, attr, sbp::FusedGeom<float, 16>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, float, 16>, attr, sbp::FusedGeom<float, 16>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, __half, 16>, attr, sbp::FusedGeom<__half, 16>::kSmem));
-        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, __half, 16>, attr, sbp::FusedGeom<__half, 16>::kSmem));
+#define SBP_FUSED_ATTR(S, R, W)                                                                               \
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<true, S, R, W>, attr, sbp::FusedGeom<S, R, W>::kSmem)); \
+        SBP_CUDA(cudaFuncSetAttribute(sbp::fused_interior<false, S, R, W>, attr, sbp::FusedGeom<S, R, W>::kSmem))
+        SBP_FUSED_ATTR(float, 8, 64);
+        SBP_FUSED_ATTR(float, 16, 64);
+        SBP_FUSED_ATTR(float, 8, 128);
+        SBP_FUSED_ATTR(float, 12, 128);
+        SBP_FUSED_ATTR(__half, 8, 64);
+        SBP_FUSED_ATTR(__half, 16, 64);
+        SBP_FUSED_ATTR(__half, 8, 128);
+        SBP_FUSED_ATTR(__half, 12, 128);
+#undef SBP_FUSED_ATTR
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched<8>, attr, sbp::FusedGeom<float, 8>::kSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::fused_batched<16>, attr, sbp::FusedGeom<float, 16>::kSmem));
         SBP_CUDA(cudaFuncSetAttribute(sbp::persistent_batched, attr, sbp::kFusedSmem));
         done[dev] = true;
     }
     return SBP_OK;
+}
+
+template <typename S, int R, int W>
+void launch_fused_tile(sbp_sim *s, const sbp::FusedParamsT<S> &fp, int old)
+{
+    using Gm = sbp::FusedGeom<S, R, W>;
+    if (fp.nsrc > 0)
+        sbp::fused_interior<true, S, R, W><<<s->fused_grid, Gm::kWarps * 32, Gm::kSmem, s->stream>>>(s->maps[old], fp);
+    else
+        sbp::fused_interior<false, S, R, W><<<s->fused_grid, Gm::kWarps * 32, Gm::kSmem, s->stream>>>(s->maps[old], fp);
 }
 
 // The one-pass interior step (old set -> new set).
@@ -646,18 +695,12 @@ int launch_fused_interior_t(sbp_sim *s)
     if (rc) return rc;
     rc = set_fused_smem_attr();
     if (rc) return rc;
-    if (s->fused_rows == 16) {
-        constexpr int smem = sbp::FusedGeom<S, 16>::kSmem;
-        if (fp.nsrc > 0)
-            sbp::fused_interior<true, S, 16><<<s->fused_grid, 16 * 32, smem, s->stream>>>(s->maps[old], fp);
-        else
-            sbp::fused_interior<false, S, 16><<<s->fused_grid, 16 * 32, smem, s->stream>>>(s->maps[old], fp);
+    if (s->fused_width == 128) {
+        if (s->fused_rows == 12) launch_fused_tile<S, 12, 128>(s, fp, old);
+        else launch_fused_tile<S, 8, 128>(s, fp, old);
     } else {
-        constexpr int smem = sbp::FusedGeom<S, 8>::kSmem;
-        if (fp.nsrc > 0)
-            sbp::fused_interior<true, S, 8><<<s->fused_grid, 8 * 32, smem, s->stream>>>(s->maps[old], fp);
-        else
-            sbp::fused_interior<false, S, 8><<<s->fused_grid, 8 * 32, smem, s->stream>>>(s->maps[old], fp);
+        if (s->fused_rows == 16) launch_fused_tile<S, 16, 64>(s, fp, old);
+        else launch_fused_tile<S, 8, 64>(s, fp, old);
     }
     SBP_CUDA(cudaGetLastError());
     return SBP_OK;
@@ -994,17 +1037,19 @@ int check_error_flag(sbp_sim *s)
     return v ? SBP_ETIMEOUT : SBP_OK;
 }
 
-// Tile of the one-pass step: rows (8 or 16) and z-block depth; new rows
-// re-encode the TMA maps (their boxes are rows high).
-int set_tile(sbp_sim *s, int rows, int depth)
+// Tile of the one-pass step: width x rows (tile_valid) and z-block depth; a
+// new width or row count re-encodes the TMA maps (their boxes have its shape).
+int set_tile(sbp_sim *s, int width, int rows, int depth)
 {
+    if (!tile_valid(width, rows) || depth <= 0) return SBP_EINVAL;
     s->fused_kchunk = depth;
-    if (rows != s->fused_rows) {
+    if (rows != s->fused_rows || width != s->fused_width) {
         s->fused_rows = rows;
+        s->fused_width = width;
         int rc = encode_maps(s);
         if (rc) return rc;
     }
-    s->fused_grid = fused_dims(s->n, rows, depth);
+    s->fused_grid = fused_dims(s->n, width, rows, depth);
     return SBP_OK;
 }
 
@@ -1034,14 +1079,25 @@ int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
     Trace trace("sbp_autotune");
     if (!s->fused_ok || linked_to_other(s)) return SBP_ESTATE;
     const int span = s->n[2] - 5;                      // interior E planes of the one-pass step
-    std::vector<std::pair<int, int>> cand;             // (rows, depth)
-    for (int rows : {8, 16}) {
-        if (rows == 16 && s->n[1] - 5 < 15) continue;  // no full 16-row tile
+    std::vector<TileChoice> cand;
+    const int shapes[4][2] = {{64, 8}, {64, 16}, {128, 8}, {128, 12}};   // (width, rows)
+    for (const auto &sh : shapes) {
+        if (sh[1] > 8 && s->n[1] - 5 < sh[1] - 1) continue;      // no full tile of that height
+        if (sh[0] > 64 && s->n[0] - 5 < sh[0] - 1) continue;     // nor of that width
         for (int c : {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256})
-            if (c <= span || c == 8) cand.push_back(std::make_pair(rows, c));
+            if (c <= span || c == 8) {
+                TileChoice t;
+                t.width = sh[0]; t.rows = sh[1]; t.depth = c;
+                cand.push_back(t);
+            }
     }
-    const std::pair<int, int> keep = std::make_pair(s->fused_rows, s->fused_kchunk);
-    if (std::find(cand.begin(), cand.end(), keep) == cand.end()) cand.push_back(keep);
+    TileChoice keep;
+    keep.width = s->fused_width; keep.rows = s->fused_rows; keep.depth = s->fused_kchunk;
+    auto same = [](const TileChoice &a, const TileChoice &b) {
+        return a.width == b.width && a.rows == b.rows && a.depth == b.depth;
+    };
+    if (std::none_of(cand.begin(), cand.end(), [&](const TileChoice &c) { return same(c, keep); }))
+        cand.push_back(keep);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     SBP_CUDA(cudaEventCreate(&e0));
     if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -1049,29 +1105,29 @@ int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
         cudaEventDestroy(e0);
         return SBP_ECUDA;
     }
-    std::pair<int, int> best = keep;
+    TileChoice best = keep;
     int rc = SBP_OK;
     float best_t = 0.f;
     for (const auto &c : cand) {
-        if ((rc = set_tile(s, c.first, c.second))) break;
+        if ((rc = set_tile(s, c.width, c.rows, c.depth))) break;
         float t = 0.f;
         if ((rc = time_trials(s, trials, e0, e1, &t))) break;
         if (best_t == 0.f || t < best_t) { best_t = t; best = c; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const std::pair<int, int> fin = rc ? keep : best;
-    const int rc2 = set_tile(s, fin.first, fin.second);
+    const TileChoice fin = rc ? keep : best;
+    const int rc2 = set_tile(s, fin.width, fin.rows, fin.depth);
     if (rc) return rc;
     if (rc2) return rc2;
     if ((rc = check_error_flag(s))) return rc;
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         read_tune_file();
-        g_tuned[std::make_tuple(s->n[0], s->n[1], s->n[2], s->prec)] = std::make_pair(best.second, best.first);
-        append_tune_file(s->n[0], s->n[1], s->n[2], s->prec, best.second, best.first);
+        g_tuned[std::make_tuple(s->n[0], s->n[1], s->n[2], s->prec)] = best;
+        append_tune_file(s->n[0], s->n[1], s->n[2], s->prec, best);
     }
-    if (chosen) *chosen = best.second;
+    if (chosen) *chosen = best.depth;
     if (best_ms) *best_ms = best_t;
     return SBP_OK;
 }
@@ -1174,9 +1230,11 @@ int batch_rebuild(sbp_batch *b)
         sbp_sim *s = b->m[g].s;
         sbp::BatchGrid &G = hg[g];
         std::memset(static_cast<void *>(&G), 0, sizeof(G));
-        // every member runs the batch's tile height (its TMA boxes are re-encoded
-        // when it differs from the member's own)
-        if (s->fused_rows != rows && (rc = set_tile(s, rows, s->fused_kchunk))) return rc;
+        // every member runs the batch's tile: 64 columns and the batch's height
+        // (its TMA boxes are re-encoded when that differs from the member's own)
+        if ((s->fused_rows != rows || s->fused_width != sbp::kFTX) &&
+            (rc = set_tile(s, sbp::kFTX, rows, s->fused_kchunk)))
+            return rc;
         for (int c = 0; c < 2; c++) {
             G.maps[c] = s->maps[c];
             if ((rc = make_fused_params(s, c, G.fp[c]))) return rc;
@@ -1520,12 +1578,13 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
     return step_timed(s, nsteps, avg_ms, launches, n_out);
 }
 
-int sbp_tile(const sbp_sim *s, int *rows, int *depth)
+int sbp_tile(const sbp_sim *s, int *rows, int *depth, int *width)
 {
     if (!s) return SBP_EINVAL;
     if (!s->fused_ok) return SBP_ESTATE;
     if (rows) *rows = s->fused_rows;
     if (depth) *depth = s->fused_kchunk;
+    if (width) *width = s->fused_width;
     return SBP_OK;
 }
 

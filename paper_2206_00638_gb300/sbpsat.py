@@ -107,7 +107,7 @@ def lib():
                 "sbp_half_step_h": (I, [pp, I]),
                 "sbp_half_step_e": (I, [pp, I]),
                 "sbp_autotune": (I, [P, I, C.POINTER(C.c_int), C.POINTER(D)]),
-                "sbp_tile": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+                "sbp_tile": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
                 "sbp_connect_phase": (I, [P, P, I, D]),
                 "sbp_checkpoint_bytes": (SZ, [P]),
                 "sbp_save": (I, [P, P, SZ]),
@@ -306,17 +306,18 @@ class Sim:
         return {k: (ms[q], cnt[q]) for q, k in enumerate(self.KERNELS) if cnt[q]}
 
     def autotune(self, trial_steps=5):
-        """Choose the tile of the one-pass step (8 or 16 rows, z-block depth) by timing
-        candidates (state unchanged); returns (depth, ms per step); ``tile`` gives the rows."""
+        """Choose the tile of the one-pass step (64 x 8 / 64 x 16 / 128 x 8 / 128 x 12 H
+        nodes, z-block depth) by timing candidates (state unchanged); returns (depth, ms per
+        step); ``tile`` gives the whole tile."""
         depth, ms = C.c_int(), C.c_double()
         _check(lib().sbp_autotune(self._h, int(trial_steps), C.byref(depth), C.byref(ms)), "sbp_autotune")
         return depth.value, ms.value
 
     def tile(self):
-        """(rows, depth) of the one-pass step's tile."""
-        rows, depth = C.c_int(), C.c_int()
-        _check(lib().sbp_tile(self._h, C.byref(rows), C.byref(depth)), "sbp_tile")
-        return rows.value, depth.value
+        """(rows, depth, width) of the one-pass step's tile."""
+        rows, depth, width = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().sbp_tile(self._h, C.byref(rows), C.byref(depth), C.byref(width)), "sbp_tile")
+        return rows.value, depth.value, width.value
 
     def save(self) -> bytes:
         """Checkpoint: the simulation's state as bytes (sbp_save)."""

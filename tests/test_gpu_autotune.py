@@ -53,6 +53,7 @@ def test_sixteen_row_tiles_bitwise_equal_eight_rows(precision, n, monkeypatch):
     """The 16-row tile (512 threads, one CTA per SM) computes every node with the same
     formula as the 8-row tile: fields and probes bit-identical, ragged last rows included."""
     w = wl.random_box(n, faces=(A, P, M, A, P, M), seed=19, steps=29)
+    monkeypatch.setenv("SBP_FUSED_WIDTH", "64")
     monkeypatch.setenv("SBP_FUSED_ROWS", "16")
     big = sbpsat.from_workload(w, precision=precision)[0]
     monkeypatch.setenv("SBP_FUSED_ROWS", "8")
@@ -68,10 +69,35 @@ def test_sixteen_row_tiles_bitwise_equal_eight_rows(precision, n, monkeypatch):
     small.close()
 
 
+@pytest.mark.parametrize("precision", [sbpsat.FP32, sbpsat.FP32_FP16STORE])
+@pytest.mark.parametrize("rows", [8, 12])
+@pytest.mark.parametrize("n", [(70, 43, 37), (140, 30, 21), (300, 26, 13), (8, 9, 10)])
+def test_wide_tiles_bitwise_equal_narrow_tiles(precision, rows, n, monkeypatch):
+    """128-column tiles (two warps per row) compute every node with the same formula as
+    the 64-column tile: fields and probes bit-identical, with ragged last columns and rows,
+    tiles wider than the grid, and a grid three tiles wide."""
+    w = wl.random_box(n, faces=(A, P, M, A, P, M), seed=23, steps=31)
+    monkeypatch.setenv("SBP_FUSED_WIDTH", "128")
+    monkeypatch.setenv("SBP_FUSED_ROWS", str(rows))
+    wide = sbpsat.from_workload(w, precision=precision)[0]
+    monkeypatch.setenv("SBP_FUSED_WIDTH", "64")
+    monkeypatch.setenv("SBP_FUSED_ROWS", "8")
+    narrow = sbpsat.from_workload(w, precision=precision)[0]
+    assert wide.tile()[2] == 128 and wide.tile()[0] == rows and narrow.tile()[2] == 64
+    for s in (wide, narrow):
+        s.reserve_probes(31)
+        s.step(31)
+    for c in range(6):
+        assert np.array_equal(wide.field(c), narrow.field(c)), c
+    assert np.array_equal(wide.probes(), narrow.probes())
+    wide.close()
+    narrow.close()
+
+
 def test_autotune_reports_tile():
-    w = wl.random_box((40, 48, 44), seed=3, steps=4)
+    w = wl.random_box((140, 48, 44), seed=3, steps=4)
     s = sbpsat.from_workload(w)[0]
     depth, _ = s.autotune(2)
-    rows, d2 = s.tile()
-    assert rows in (8, 16) and d2 == depth
+    rows, d2, width = s.tile()
+    assert (width, rows) in ((64, 8), (64, 16), (128, 8), (128, 12)) and d2 == depth
     s.close()

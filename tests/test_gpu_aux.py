@@ -95,9 +95,10 @@ def test_autotune_result_file(tmp_path):
             "print(*s.tile())\n" % ROOT)
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
     assert out.returncode == 0, out.stderr
-    tile_rows, depth = (int(v) for v in out.stdout.strip().splitlines()[-1].split())
+    tile_rows, depth, width = (int(v) for v in out.stdout.strip().splitlines()[-1].split())
     lines = [json.loads(l) for l in path.read_text().splitlines() if l.strip()]
-    assert {"nx": 70, "ny": 43, "nz": 61, "precision": 0, "depth": depth, "rows": tile_rows} in lines
+    assert {"nx": 70, "ny": 43, "nz": 61, "precision": 0, "depth": depth, "rows": tile_rows,
+            "width": width} in lines
     # a later process creates the same shape with the tuned tile
     code2 = ("import sys; sys.path.insert(0, %r)\n"
              "from paper_2206_00638_gb300 import sbpsat, workloads as wl\n"
@@ -105,4 +106,4 @@ def test_autotune_result_file(tmp_path):
              "print(*s.tile())\n" % ROOT)
     out2 = subprocess.run([sys.executable, "-c", code2], env=env, capture_output=True, text=True, timeout=300)
     assert out2.returncode == 0, out2.stderr
-    assert out2.stdout.strip().splitlines()[-1].split() == [str(tile_rows), str(depth)]
+    assert out2.stdout.strip().splitlines()[-1].split() == [str(tile_rows), str(depth), str(width)]

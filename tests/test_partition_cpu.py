@@ -22,9 +22,12 @@ def extents(n, c):
     return tuple(n[a] + (1 if ON_PLUS[c][a] else 2) for a in range(3))
 
 
-def fused_nodes(n, depth, rows=FTY):
-    """(H nodes, E nodes) the one-pass kernel stores, as lists of (i, j, k) (one entry per store)."""
+def fused_nodes(n, depth, rows=FTY, width=FTX):
+    """(H nodes, E nodes) the one-pass kernel stores, as lists of (i, j, k) (one entry per store).
+    A tile is `width` columns by `rows` rows; with 128 columns two warps share a row, warp
+    group g taking columns 64 g .. 64 g + 63 of it."""
     nx, ny, nz = n
+    FTX = width
     tx = (nx - 5 + FTX - 2) // (FTX - 1)
     ty = (ny - 5 + rows - 2) // (rows - 1)
     tz = (nz - 5 + depth - 1) // depth
@@ -36,7 +39,8 @@ def fused_nodes(n, depth, rows=FTY):
             j = y0 + w
             row_e = w < rows - 1 and j <= ny - 3
             row_h = j <= ny - 2 and (w < rows - 1 or j == ny - 2)
-            for c in range(FTX):
+            for g, lane, h in itertools.product(range(FTX // 64), range(32), range(2)):
+                c = 64 * g + lane + 32 * h
                 i = x0 + c
                 col_h = row_h and i <= nx - 2 and (c < FTX - 1 or i == nx - 2)
                 col_e = row_e and c < FTX - 1 and i <= nx - 3
@@ -115,14 +119,14 @@ def _counts(n, comps, written):
 
 
 GRIDS = [((66, 9, 9), 8), ((67, 9, 10), 8), ((128, 9, 9), 16), ((129, 10, 9), 8), ((8, 8, 8), 8), ((9, 12, 13), 8), ((10, 13, 21), 13), ((68, 12, 17), 8), ((69, 20, 9), 8),
-         ((70, 19, 33), 13), ((40, 11, 40), 64)]
+         ((70, 19, 33), 13), ((40, 11, 40), 64), ((132, 9, 9), 8), ((133, 15, 9), 8), ((259, 9, 10), 16)]
 
 
-@pytest.mark.parametrize("rows", [8, 16])
+@pytest.mark.parametrize("width, rows", [(64, 8), (64, 16), (128, 8), (128, 12)])
 @pytest.mark.parametrize("n, depth", GRIDS)
-def test_every_node_written_once(n, depth, rows):
-    """rows: H rows per one-pass tile (8 or 16 warps)."""
-    fh, fe = fused_nodes(n, depth, rows)
+def test_every_node_written_once(n, depth, width, rows):
+    """A one-pass tile of width x rows H nodes (the four tiles the host accepts)."""
+    fh, fe = fused_nodes(n, depth, rows, width)
     bh, be = band_nodes(n, 4), band_nodes(n, 3)
     for nodes in (fh, fe, bh, be):                                  # no kernel writes a node twice
         assert len(nodes) == len(set(nodes))
