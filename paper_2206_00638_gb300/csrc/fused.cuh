@@ -158,6 +158,20 @@ __device__ __forceinline__ void issue_plane(const FusedMaps &m, unsigned char *s
 
 // One CTA of the one-pass interior step: tile (bx, by) in x/y, z-chunk bz,
 // time step `step` (J is evaluated at t^{step+1/2}), probe sample `pslot`.
+// A value rounded to the storage type once: the FP32 value later arithmetic
+// reads (FP16 storage: the stored half, widened) and the stored element.
+template <typename S> struct Rounded { float f; S s; };
+template <typename S>
+__device__ __forceinline__ Rounded<S> rounded(float v)
+{
+    if constexpr (std::is_same<S, __half>::value) {
+        const __half h = __float2half_rn(v);
+        return {__half2float(h), h};
+    } else {
+        return {v, v};
+    }
+}
+
 template <bool SRC, typename S, int R = kFTY, int W = kFTX>
 __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedParamsT<S> &p, long long step,
                                            long long pslot, int bx, int by, int bz, unsigned char *smem)
@@ -302,16 +316,17 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             bz.add(By, exq - ex_jm);    bz.add(Bx, eyq - ey_im, -1.f);
             // the values the stores keep (FP16 storage rounds here, and E
             // below uses the rounded H, as a separate E half-step would)
-            const float hx = quant<S>(ld_s(H0 + rh) + plain_increment(bx));
-            const float hy = quant<S>(ld_s(H1 + rh) + plain_increment(by));
-            const float hz = quant<S>(ld_s(H2 + rh) + plain_increment(bz));
+            const Rounded<S> rhx = rounded<S>(ld_s(H0 + rh) + plain_increment(bx));
+            const Rounded<S> rhy = rounded<S>(ld_s(H1 + rh) + plain_increment(by));
+            const Rounded<S> rhz = rounded<S>(ld_s(H2 + rh) + plain_increment(bz));
+            const float hx = rhx.f, hy = rhy.f, hz = rhz.f;
             Hq[(0 * kFTY + w) * kFTX + c] = hx;
             Hq[(1 * kFTY + w) * kFTX + c] = hy;
             Hq[(2 * kFTY + w) * kFTX + c] = hz;
             if (colH[h] && (q < k1 || q == nz - 2)) {
-                st_s(oH0 + obase[h], hx);
-                st_s(oH1 + obase[h], hy);
-                st_s(oH2 + obase[h], hz);
+                oH0[obase[h]] = rhx.s;
+                oH1[obase[h]] = rhy.s;
+                oH2[obase[h]] = rhz.s;
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
@@ -359,12 +374,13 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                         else az.add(p.AJ, J, -1.f);
                     }
                 }
-                const float ex = quant<S>(ec[h][0] + scaled_increment(ax, sx));
-                const float ey = quant<S>(ec[h][1] + scaled_increment(ay, sy));
-                const float ez = quant<S>(ec[h][2] + scaled_increment(az, sz));
-                st_s(oE0 + obase[h], ex);
-                st_s(oE1 + obase[h], ey);
-                st_s(oE2 + obase[h], ez);
+                const Rounded<S> rex = rounded<S>(ec[h][0] + scaled_increment(ax, sx));
+                const Rounded<S> rey = rounded<S>(ec[h][1] + scaled_increment(ay, sy));
+                const Rounded<S> rez = rounded<S>(ec[h][2] + scaled_increment(az, sz));
+                const float ex = rex.f, ey = rey.f, ez = rez.f;
+                oE0[obase[h]] = rex.s;
+                oE1[obase[h]] = rey.s;
+                oE2[obase[h]] = rez.s;
                 if (pmask[h]) {
                     unsigned long long m = pmask[h];
                     while (m) {
