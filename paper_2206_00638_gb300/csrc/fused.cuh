@@ -639,8 +639,10 @@ __device__ __forceinline__ void band_h_warp(const Params<T, S> &p, const Band &b
     if (pm) band_probes(p, pm, 3, i, j, pslot, hn, have);
 }
 
+// At most 56 registers: two 256-thread CTAs then fit on an SM beside a 512-thread
+// one-pass CTA (band H runs concurrently with it), without spills.
 template <typename T, bool MUVAR, typename S>
-__global__ void __launch_bounds__(256) band_h(const Params<T, S> p, const Band b, S *hx_out, S *hy_out, S *hz_out)
+__global__ void __maxnreg__(56) band_h(const Params<T, S> p, const Band b, S *hx_out, S *hy_out, S *hz_out)
 {
     const unsigned w = blockIdx.x * 8u + (threadIdx.x >> 5);
     if (w >= b.wz + b.wy + b.wx) return;
