@@ -316,8 +316,9 @@ def run_ours(args):
         e2e = {"value": cells * n_e2e / (t1 - t0) / 1e9, "unit": "Gcell-updates/s",
                "h2d_bytes_per_step": h2d / n_e2e, "d2h_bytes_per_step": d2h / n_e2e,
                "seconds": t1 - t0, "steps": n_e2e,
-               "what": "creation, material and initial-field upload from pinned host memory, the workload's "
-                       "steps, probe samples and one field back to the host"}
+               "what": "creation (material cells from pageable host memory), initial-field upload from "
+                       "pinned host memory, the workload's steps, probe samples and one field back to pinned "
+                       "host memory"}
         s2.close()
 
     serving = None

@@ -16,6 +16,7 @@
 // in-place h_update / e_update pair on the current set.
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <climits>
 #include <cstdint>
 
@@ -183,10 +184,16 @@ bool desc_valid(const sbp_grid_desc *d)
     }
     const long long cells = (long long)d->nx * d->ny * d->nz;
     if (cells > (1ll << 34)) return false;
+    // every cell finite and >= 1e-3 (NaN fails both comparisons); a branch-free
+    // pass, so that the compiler vectorises it (a 512^3 grid has 1.3e8 cells)
     for (const float *m : {d->eps_r, d->mu_r}) {
         if (!m) continue;
-        for (long long q = 0; q < cells; q++)
-            if (!(m[q] >= 1e-3f) || !std::isfinite(m[q])) return false;
+        unsigned bad = 0u;
+        for (long long q = 0; q < cells; q++) {
+            const float v = m[q];
+            bad |= (unsigned)!(v >= 1e-3f) | (unsigned)!(v <= FLT_MAX);
+        }
+        if (bad) return false;
     }
     return true;
 }
@@ -1354,6 +1361,40 @@ int batch_sample_energy(sbp_batch *b, sbp_batch::Member &m)
 
 }  // namespace
 
+namespace sbp {
+
+// A dense (e0, e1, e2) field into the padded layout (row pitch sy, plane pitch
+// sz) and back: host copies go through a contiguous staging array, so the DMA
+// moves one block instead of e1 * e2 short rows.
+template <typename T>
+__global__ void put_field(const T *__restrict__ src, int e0, int e1, int e2, T *__restrict__ dst, long long sy,
+                          long long sz)
+{
+    const long long total = (long long)e0 * e1 * e2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % e0);
+        const int j = (int)((q / e0) % e1);
+        const int k = (int)(q / ((long long)e0 * e1));
+        dst[(long long)k * sz + (long long)j * sy + i] = src[q];
+    }
+}
+template <typename T>
+__global__ void get_field(const T *__restrict__ src, int e0, int e1, int e2, long long sy, long long sz,
+                          T *__restrict__ dst)
+{
+    const long long total = (long long)e0 * e1 * e2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q % e0);
+        const int j = (int)((q / e0) % e1);
+        const int k = (int)(q / ((long long)e0 * e1));
+        dst[q] = src[(long long)k * sz + (long long)j * sy + i];
+    }
+}
+
+}  // namespace sbp
+
 extern "C" {
 
 size_t sbp_workspace_bytes(const sbp_grid_desc *desc)
@@ -1439,6 +1480,23 @@ int sbp_set_field(sbp_sim *s, int comp, const void *src, int is_device)
         if (!is_device) SBP_CUDA(cudaStreamSynchronize(s->stream));
         return SBP_OK;
     }
+    if (!is_device && s->fused_ok) {
+        // host values: one contiguous copy into the spare set's array of this
+        // component (dead between steps: the next step overwrites it), then a
+        // scatter into the padded layout
+        const size_t bytes = (size_t)e[0] * e[1] * e[2] * s->esize;
+        void *stage = s->set[s->cur ^ 1][comp];
+        SBP_CUDA(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, s->stream));
+        if (s->esize == 8)
+            sbp::put_field<double><<<1024, 256, 0, s->stream>>>(static_cast<const double *>(stage), e[0], e[1], e[2],
+                                                               static_cast<double *>(s->set[s->cur][comp]), s->sy, s->sz);
+        else
+            sbp::put_field<float><<<1024, 256, 0, s->stream>>>(static_cast<const float *>(stage), e[0], e[1], e[2],
+                                                              static_cast<float *>(s->set[s->cur][comp]), s->sy, s->sz);
+        SBP_CUDA(cudaGetLastError());
+        SBP_CUDA(cudaStreamSynchronize(s->stream));
+        return SBP_OK;
+    }
     cudaMemcpy3DParms m = {};
     m.srcPtr = make_cudaPitchedPtr(const_cast<void *>(src), e[0] * s->esize, e[0] * s->esize, e[1]);
     m.dstPtr = make_cudaPitchedPtr(s->set[s->cur][comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);
@@ -1469,6 +1527,22 @@ int sbp_get_field(sbp_sim *s, int comp, void *dst, int to_device)
             return check_error_flag(s);
         }
         return SBP_OK;
+    }
+    if (!to_device && s->fused_ok) {
+        // gather into the spare set's array (dead between steps), then one
+        // contiguous copy to the host
+        const size_t bytes = (size_t)e[0] * e[1] * e[2] * s->esize;
+        void *stage = s->set[s->cur ^ 1][comp];
+        if (s->esize == 8)
+            sbp::get_field<double><<<1024, 256, 0, s->stream>>>(static_cast<const double *>(s->set[s->cur][comp]), e[0],
+                                                               e[1], e[2], s->sy, s->sz, static_cast<double *>(stage));
+        else
+            sbp::get_field<float><<<1024, 256, 0, s->stream>>>(static_cast<const float *>(s->set[s->cur][comp]), e[0],
+                                                              e[1], e[2], s->sy, s->sz, static_cast<float *>(stage));
+        SBP_CUDA(cudaGetLastError());
+        SBP_CUDA(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDeviceToHost, s->stream));
+        SBP_CUDA(cudaStreamSynchronize(s->stream));
+        return check_error_flag(s);
     }
     cudaMemcpy3DParms m = {};
     m.srcPtr = make_cudaPitchedPtr(s->set[s->cur][comp], s->sy * s->esize, e[0] * s->esize, s->n[1] + 2);

@@ -59,6 +59,32 @@ def test_strerror_and_workspace_bytes_without_gpu():
     assert L.sbp_workspace_bytes(ctypes.byref(d)) > 0
 
 
+@pytest.mark.parametrize("bad", [float("nan"), float("inf"), -float("inf"), 0.0, -2.0, 9.9e-4])
+@pytest.mark.parametrize("which", ["eps_r", "mu_r"])
+def test_workspace_bytes_rejects_bad_material_cells(bad, which):
+    """Every eps_r / mu_r cell must be finite and >= 1e-3; one bad cell anywhere (here the
+    last, and one in the middle of a run of good cells) rejects the grid."""
+    import numpy as np
+    from paper_2206_00638_gb300 import sbpsat
+    L = sbpsat.lib()
+    d = sbpsat.GridDesc()
+    d.nx, d.ny, d.nz = 17, 9, 10
+    d.dx = d.dy = d.dz = 1e-3
+    d.cfl_fraction = 0.9
+    d.precision = 0
+    for f in range(6):
+        d.face[f] = 0
+    cells = np.full(17 * 9 * 10, 2.5, dtype=np.float32)
+    cells[:5] = 1e-3                          # the smallest accepted value
+    setattr(d, which, cells.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+    assert L.sbp_workspace_bytes(ctypes.byref(d)) > 0
+    for pos in (cells.size - 1, 777):
+        c2 = cells.copy()
+        c2[pos] = bad
+        setattr(d, which, c2.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        assert L.sbp_workspace_bytes(ctypes.byref(d)) == 0, (bad, pos)
+
+
 def test_no_cpu_fallback_in_product_path():
     """The binding never imports the oracle (the only CPU implementation)."""
     src = open(os.path.join(ROOT, "paper_2206_00638_gb300", "sbpsat.py")).read()
