@@ -552,6 +552,8 @@ def run_blocks(args):
     sims = sbpsat.from_workload(w, stream=stream, precision=prec)
     for s in sims:
         s.reserve_probes(args.warmup + args.steps + 8)
+        if prec != sbpsat.FP64 and not args.no_autotune:
+            s.autotune(5)
     sbpsat.step_group(sims, args.warmup)
     torch.cuda.synchronize()
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

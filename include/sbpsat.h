@@ -225,9 +225,10 @@ int sbp_step_timed(sbp_sim *s, int64_t nsteps, double *avg_ms, int64_t *launches
  * simulations created later in the process (and written to the file named by
  * SBP_TUNE_CACHE, if set).  *chosen_depth and *ms_per_step (optional) receive
  * the depth and its time; sbp_tile reports the whole tile.  Synchronises the
- * stream.  Errors: SBP_EINVAL, SBP_ESTATE (the grid does not run the
- * one-pass step, or has an interface to another block), SBP_ECUDA,
- * SBP_ETIMEOUT.  A batch runs all its members on one tile, 64 columns wide:
+ * stream.  A block joined to others by interface faces may be tuned: its
+ * trial steps read the partners' current fields and write nothing of theirs.
+ * Errors: SBP_EINVAL, SBP_ESTATE (the grid does not run the one-pass step),
+ * SBP_ECUDA, SBP_ETIMEOUT.  A batch runs all its members on one tile, 64 columns wide:
  * 16 rows when every member has at least 20 cells along y and the batch steps
  * with three launches per step, else 8 (the environment variable
  * SBP_FUSED_ROWS=8 forces 8); a member's own tile is changed to it when the

@@ -1084,7 +1084,9 @@ int time_trials(sbp_sim *s, int trials, cudaEvent_t e0, cudaEvent_t e1, float *m
 int autotune(sbp_sim *s, int trials, int *chosen, double *best_ms)
 {
     Trace trace("sbp_autotune");
-    if (!s->fused_ok || linked_to_other(s)) return SBP_ESTATE;
+    // a block joined to others tunes too: its trial steps read the partners' current
+    // fields at the interface and write only this block's spare set
+    if (!s->fused_ok) return SBP_ESTATE;
     const int span = s->n[2] - 5;                      // interior E planes of the one-pass step
     std::vector<TileChoice> cand;
     const int shapes[4][2] = {{64, 8}, {64, 16}, {128, 8}, {128, 12}};   // (width, rows)

@@ -101,3 +101,28 @@ def test_autotune_reports_tile():
     rows, d2, width = s.tile()
     assert (width, rows) in ((64, 8), (64, 16), (128, 8), (128, 12)) and d2 == depth
     s.close()
+
+
+def test_autotune_of_joined_blocks_changes_nothing():
+    """Blocks joined by the interface SAT can be tuned: the tuned group steps bit-identically
+    to an untuned copy, and the partner's fields are untouched by the trials."""
+    w = wl.two_block(nxy=40, nz=24, steps=30)
+    tuned = sbpsat.from_workload(w)
+    plain = sbpsat.from_workload(w)
+    for g in (tuned, plain):
+        for s in g:
+            s.reserve_probes(30)
+        sbpsat.step_group(g, 5)
+    before = [tuned[1].field(c) for c in range(6)]
+    depth, ms = tuned[0].autotune(2)
+    assert depth >= 8 and ms > 0 and tuned[0].step_index == 5
+    for c in range(6):
+        assert np.array_equal(tuned[1].field(c), before[c]), c
+    for g in (tuned, plain):
+        sbpsat.step_group(g, 25)
+    for a, b in zip(tuned, plain):
+        for c in range(6):
+            assert np.array_equal(a.field(c), b.field(c)), c
+        assert np.array_equal(a.probes(), b.probes())
+    for s in tuned + plain:
+        s.close()
