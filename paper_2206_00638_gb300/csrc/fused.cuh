@@ -310,7 +310,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
             const float exq = ld_s(E0 + re), ex_jm = ld_s(E0 + re - kBX);
             const float eyq = ld_s(E1 + re), ey_im = ld_s(E1 + re - 1);
             const float ezq = ld_s(E2 + re), ez_im = ld_s(E2 + re - 1), ez_jm = ld_s(E2 + re - kBX);
-            Acc<float> bx, by, bz;
+            typename AccOf<float, S>::type bx, by, bz;
             bx.add(Bz, eyq - ec[h][1]); bx.add(By, ezq - ez_jm, -1.f);
             by.add(Bx, ezq - ez_im);    by.add(Bz, exq - ec[h][0], -1.f);
             bz.add(By, exq - ex_jm);    bz.add(Bx, eyq - ey_im, -1.f);
@@ -353,7 +353,7 @@ __device__ __forceinline__ void fused_body(const FusedMaps &maps, const FusedPar
                 const float hz_ip = Hp[(2 * kFTY + w) * kFTX + c + 1];
                 const float hz_jp = Hp[(2 * kFTY + w + 1) * kFTX + c];
                 const float hxp = hc[h][0], hyp = hc[h][1], hzp = hc[h][2];
-                Acc<float> ax, ay, az;
+                typename AccOf<float, S>::type ax, ay, az;
                 ax.add(Ay, hz_jp - hzp); ax.add(Az, hy - hyp, -1.f);
                 ay.add(Az, hx - hxp);    ay.add(Ax, hz_ip - hzp, -1.f);
                 az.add(Ax, hy_ip - hyp); az.add(Ay, hx_jp - hxp, -1.f);

@@ -151,6 +151,28 @@ __device__ __forceinline__ double scaled_increment(const Acc<double> &a, double 
 __device__ __forceinline__ float plain_increment(const Acc<float> &a) { return a.hi + a.lo; }
 __device__ __forceinline__ double plain_increment(const Acc<double> &a) { return a.hi; }
 
+// FP32 arithmetic on FP16-stored fields: the coefficients' rounding residue
+// (lo, about 6e-8 relative) is far below the storage rounding (4.9e-4), so
+// the increment is accumulated from the rounded coefficients alone.
+struct AccLite {
+    float hi = 0.f;
+    __device__ __forceinline__ void add(const Coef<float> &c, float x, float scale = 1.f)
+    {
+        hi = fmaf(scale * c.hi, x, hi);
+    }
+};
+__device__ __forceinline__ float scaled_increment(const AccLite &a, float s)
+{
+    float rh, rl;
+    recip_pair(s, rh, rl);
+    return fmaf(rh, a.hi, rl * a.hi);
+}
+__device__ __forceinline__ float plain_increment(const AccLite &a) { return a.hi; }
+
+// The accumulator of arithmetic type T for fields stored as S.
+template <typename T, typename S> struct AccOf { using type = Acc<T>; };
+template <> struct AccOf<float, __half> { using type = AccLite; };
+
 // Rows of the Appendix operators at unit spacing.  Every row reads at most
 // three consecutive entries of its line; they are gathered first (no branch
 // before the loads, so all of a node's loads are in flight together) and the
@@ -432,7 +454,7 @@ __device__ __forceinline__ void h_gather(const Params<T, S> &p, const int idx[3]
 template <typename T, int C, bool MUVAR, int G = 7, typename S = T>
 __device__ __forceinline__ T h_apply(const Params<T, S> &p, const int idx[3], long long o, T hold, const Tri<T> v[2])
 {
-    Acc<T> acc;
+    typename AccOf<T, S>::type acc;
     T gam = T(0);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -511,7 +533,7 @@ template <typename T, int C, bool MUVAR, bool CG = false, int G = 7, typename S 
 __device__ __forceinline__ T e_apply(const Params<T, S> &p, const int idx[3], long long o, T eold, T se, const Tri<T> v[2],
                                      unsigned smask, double t_half)
 {
-    Acc<T> acc;
+    typename AccOf<T, S>::type acc;
     T gam = T(0);
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
@@ -630,7 +652,7 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) h_update(const Params<T, S> 
                 const T dEy_z = eyc - eym, dEz_y = ezc - ez_jm;
                 const T dEz_x = ezc - ez_im, dEx_z = exc - exm;
                 const T dEx_y = exc - ex_jm, dEy_x = eyc - ey_im;
-                Acc<T> ax, ay, az;
+                typename AccOf<T, S>::type ax, ay, az;
                 ax.add(Bz, dEy_z); ax.add(By, dEz_y, T(-1));
                 ay.add(Bx, dEz_x); ay.add(Bz, dEx_z, T(-1));
                 az.add(By, dEx_y); az.add(Bx, dEy_x, T(-1));
@@ -745,7 +767,7 @@ __global__ void __launch_bounds__(kBlockX *kBlockY) e_update(const Params<T, S> 
             const T hz_ip = ldg_s(Hz + o + 1);
             const T hx_jp = ldg_s(Hx + o + p.sy);
             const T hy_ip = ldg_s(Hy + o + 1);
-            Acc<T> ax, ay, az;
+            typename AccOf<T, S>::type ax, ay, az;
             ax.add(Ay, hz_jp - hzc); ax.add(Az, hyn - hyc, T(-1));
             ay.add(Az, hxn - hxc);   ay.add(Ax, hz_ip - hzc, T(-1));
             az.add(Ax, hy_ip - hyc); az.add(Ay, hx_jp - hxc, T(-1));
